@@ -1,0 +1,277 @@
+/*
+ * xt_oracle.c -- scalar CPU oracle for banded affine-gap seed extension.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the correctness oracle that the CUDA
+ * path is checked against.  Only the tests, the smoke check and the bench's
+ * CPU-baseline leg may load it; the library never does.  It shares no code,
+ * header, table or constant with the CUDA path.
+ *
+ * What it computes (arXiv 2301.09310, Sec. II-A, Eq. 1, read as seed
+ * extension per Sec. II-A "extending to both directions from the found seeds";
+ * one direction per call):
+ *
+ *   The DP runs on an extended matrix, rows r = -1..tlen-1 (target, "reference
+ *   at i" of Eq. 1) and columns c = -1..qlen-1 (query, "query at j").
+ *   alpha = gap_open + gap_extend (cost of a gap's first base, Eq. 1's alpha),
+ *   beta  = gap_extend            (each further base,        Eq. 1's beta).
+ *
+ *   band      : cell (r,c) is in band iff |r - c| <= w; out-of-band cells are
+ *               dead (H = E = F = 0).
+ *   seed      : H(-1,-1) = h0.
+ *   row -1    : H(-1,c) = E(-1,c) = max(0, h0 - alpha - beta*c) when in band,
+ *               F(-1,c) = 0.
+ *   column -1 : H(r,-1) = F(r,-1) = max(0, h0 - alpha - beta*r) when in band,
+ *               E(r,-1) = 0.
+ *   S(i,j)    : match if t_i == q_j and both are bases A,C,G,T (codes 0..3);
+ *               n_score if either code is N (any byte >= 4 is N);
+ *               mismatch otherwise.
+ *   interior  : D = H(i-1,j-1);  M = D + S(i,j) if D > 0, else 0
+ *               (a dead cell is not restarted: the extension stays anchored at
+ *               the seed, which is how Eq. 1's "0" is read here);
+ *               E = max(0, H(i,j-1) - alpha, E(i,j-1) - beta)      (Eq. 1, E)
+ *               F = max(0, H(i-1,j) - alpha, F(i-1,j) - beta)      (Eq. 1, F)
+ *               H = max(0, M, E, F)                                (Eq. 1, H)
+ *
+ *   After each row i (in order): m_i = max in-band H(i,j) over j >= 0, mj_i =
+ *   the largest such j attaining it (m_i = 0, mj_i = -1 for an empty band).
+ *   gscore: if column qlen-1 is in band, H(i,qlen-1) > 0 and > gscore, then
+ *   gscore = H(i,qlen-1), gtle = i+1 (strict, so the earliest row wins).
+ *   local best (best,bi,bj) starts (h0,-1,-1), max_off = 0:
+ *     m_i > best           -> best = m_i, bi = i, bj = mj_i,
+ *                             max_off = max(max_off, |mj_i - i|)
+ *     else if zdrop > 0    -> d = (i-bi) - (mj_i-bj),
+ *                             stop after row i if best - m_i - |d|*beta > zdrop.
+ *   result = {best, bj+1, bi+1, gscore, gtle, max_off, OK}; gscore starts -1,
+ *   gtle 0.  qlen == 0 -> {h0,0,0,h0,0,0}; tlen == 0 -> {h0,0,0,-1,0,0}.
+ *   Useful cells = sum over rows 0..i_end of the in-band width of the row,
+ *   i_end = the last row (not after the stop row) holding an H > 0.
+ *
+ * The arithmetic is int64 throughout, so no value of the definition can
+ * overflow for the input limits the library accepts.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <pthread.h>
+
+/* Scoring record, laid out like the library's but declared here on its own. */
+typedef struct {
+  int32_t match, mismatch, gap_open, gap_extend, w, zdrop, n_score;
+} xo_scoring;
+
+enum { XO_OK = 0, XO_EINVAL = 1 };
+
+/* Input limits shared in value (not in code) with the library's checks. */
+#define XO_MAX_LEN (1 << 20)
+#define XO_MAX_H0 (1 << 20)
+
+static int64_t max2(int64_t a, int64_t b) { return a > b ? a : b; }
+static int64_t min2(int64_t a, int64_t b) { return a < b ? a : b; }
+static int64_t iabs64(int64_t a) { return a < 0 ? -a : a; }
+
+static int in_band(int64_t r, int64_t c, int64_t w) { return iabs64(r - c) <= w; }
+
+static int64_t score(const xo_scoring* sc, uint8_t a, uint8_t b) {
+  if (a >= 4 || b >= 4) return sc->n_score;
+  return a == b ? sc->match : sc->mismatch;
+}
+
+/* Number of in-band columns j in [0, qlen) of row i. */
+static int64_t band_width(int64_t i, int64_t qlen, int64_t w) {
+  int64_t lo = max2(0, i - w), hi = min2(qlen, i + w + 1);
+  return hi > lo ? hi - lo : 0;
+}
+
+/* Returns 0 when the scoring record is acceptable. */
+int xo_check_scoring(const xo_scoring* sc) {
+  if (!sc) return XO_EINVAL;
+  if (sc->match < 1 || sc->match > 127) return XO_EINVAL;
+  if (sc->mismatch > 0 || sc->mismatch < -127) return XO_EINVAL;
+  if (sc->n_score > 0 || sc->n_score < -127) return XO_EINVAL;
+  if (sc->gap_open < 0 || sc->gap_open > 1023) return XO_EINVAL;
+  if (sc->gap_extend < 0 || sc->gap_extend > 1023) return XO_EINVAL;
+  if (sc->w < 0) return XO_EINVAL;
+  return XO_OK;
+}
+
+/*
+ * One extension.  out[7] = {score, qle, tle, gscore, gtle, max_off, status}.
+ * *cells receives the useful-cell count.  When rows_m / rows_mj are non-NULL
+ * they receive m_i and mj_i for every row that was evaluated and *n_rows the
+ * number of such rows (the stop row included).  When full_H/E/F are non-NULL
+ * they receive the extended matrices, (tlen+1) x (qlen+1), row-major, entry
+ * [(r+1)*(qlen+1) + (c+1)] for cell (r,c); rows after the stop row stay 0.
+ */
+void xo_extend_one(const uint8_t* q, int32_t qlen, const uint8_t* t, int32_t tlen, int32_t h0,
+                   const xo_scoring* sc, int32_t out[7], int64_t* cells, int64_t* rows_m,
+                   int64_t* rows_mj, int32_t* n_rows, int64_t* full_H, int64_t* full_E,
+                   int64_t* full_F) {
+  const int64_t alpha = (int64_t)sc->gap_open + sc->gap_extend;
+  const int64_t beta = sc->gap_extend;
+  const int64_t w = sc->w;
+  if (n_rows) *n_rows = 0;
+  *cells = 0;
+  if (qlen == 0) {
+    out[0] = h0; out[1] = 0; out[2] = 0; out[3] = h0; out[4] = 0; out[5] = 0; out[6] = XO_OK;
+    return;
+  }
+  if (tlen == 0) {
+    out[0] = h0; out[1] = 0; out[2] = 0; out[3] = -1; out[4] = 0; out[5] = 0; out[6] = XO_OK;
+    return;
+  }
+  const int64_t ncol = (int64_t)qlen + 1; /* index c+1 holds column c */
+  int64_t* Hp = calloc((size_t)ncol, sizeof(int64_t));
+  int64_t* Ep = calloc((size_t)ncol, sizeof(int64_t));
+  int64_t* Fp = calloc((size_t)ncol, sizeof(int64_t));
+  int64_t* Hc = calloc((size_t)ncol, sizeof(int64_t));
+  int64_t* Ec = calloc((size_t)ncol, sizeof(int64_t));
+  int64_t* Fc = calloc((size_t)ncol, sizeof(int64_t));
+
+  /* Row -1: the seed cell and the insertion run along the query. */
+  Hp[0] = h0; Ep[0] = 0; Fp[0] = 0;
+  for (int64_t c = 0; c < qlen; ++c) {
+    if (in_band(-1, c, w)) {
+      int64_t v = max2(0, h0 - alpha - beta * c);
+      Hp[c + 1] = v; Ep[c + 1] = v; Fp[c + 1] = 0;
+    }
+  }
+  if (full_H) {
+    for (int64_t c = 0; c < ncol; ++c) {
+      full_H[c] = Hp[c]; full_E[c] = Ep[c]; full_F[c] = Fp[c];
+    }
+  }
+
+  int64_t best = h0, bi = -1, bj = -1, max_off = 0;
+  int64_t gscore = -1, gtle = 0;
+  int64_t last_live = -1;
+  for (int64_t i = 0; i < tlen; ++i) {
+    /* Column -1: the deletion run along the target. */
+    if (in_band(i, -1, w)) {
+      int64_t v = max2(0, h0 - alpha - beta * i);
+      Hc[0] = v; Fc[0] = v; Ec[0] = 0;
+    } else {
+      Hc[0] = 0; Fc[0] = 0; Ec[0] = 0;
+    }
+    int64_t m = 0, mj = -1;
+    int any_live = 0;
+    for (int64_t j = 0; j < qlen; ++j) {
+      if (!in_band(i, j, w)) {
+        Hc[j + 1] = 0; Ec[j + 1] = 0; Fc[j + 1] = 0;
+        continue;
+      }
+      int64_t D = Hp[j];
+      int64_t M = D > 0 ? D + score(sc, t[i], q[j]) : 0;
+      int64_t E = max2(0, max2(Hc[j] - alpha, Ec[j] - beta));
+      int64_t F = max2(0, max2(Hp[j + 1] - alpha, Fp[j + 1] - beta));
+      int64_t H = max2(max2(0, M), max2(E, F));
+      Hc[j + 1] = H; Ec[j + 1] = E; Fc[j + 1] = F;
+      if (H >= m) { m = H; mj = j; }
+      if (H > 0) any_live = 1;
+    }
+    if (full_H) {
+      for (int64_t c = 0; c < ncol; ++c) {
+        full_H[(i + 1) * ncol + c] = Hc[c];
+        full_E[(i + 1) * ncol + c] = Ec[c];
+        full_F[(i + 1) * ncol + c] = Fc[c];
+      }
+    }
+    if (rows_m) { rows_m[i] = m; rows_mj[i] = mj; }
+    if (n_rows) *n_rows = (int32_t)(i + 1);
+    if (any_live) last_live = i;
+    /* End-to-end score at the last query column. */
+    if (in_band(i, qlen - 1, w)) {
+      int64_t g = Hc[qlen];
+      if (g > 0 && g > gscore) { gscore = g; gtle = i + 1; }
+    }
+    /* Local best and z-drop, in row order. */
+    if (m > best) {
+      best = m; bi = i; bj = mj;
+      max_off = max2(max_off, iabs64(mj - i));
+    } else if (sc->zdrop > 0) {
+      int64_t d = (i - bi) - (mj - bj);
+      int64_t drop = best - m - iabs64(d) * beta;
+      if (drop > sc->zdrop) break;
+    }
+    int64_t* tmp;
+    tmp = Hp; Hp = Hc; Hc = tmp;
+    tmp = Ep; Ep = Ec; Ec = tmp;
+    tmp = Fp; Fp = Fc; Fc = tmp;
+  }
+  int64_t n = 0;
+  for (int64_t i = 0; i <= last_live; ++i) n += band_width(i, qlen, w);
+  *cells = n;
+  out[0] = (int32_t)best; out[1] = (int32_t)(bj + 1); out[2] = (int32_t)(bi + 1);
+  out[3] = (int32_t)gscore; out[4] = (int32_t)gtle; out[5] = (int32_t)max_off; out[6] = XO_OK;
+  free(Hp); free(Ep); free(Fp); free(Hc); free(Ec); free(Fc);
+}
+
+/* Per-pair input checks; returns XO_OK or XO_EINVAL. */
+static int check_pair(int64_t qo, int32_t ql, int64_t q_bytes, int64_t to, int32_t tl,
+                      int64_t t_bytes, int32_t h0) {
+  if (h0 < 1 || h0 > XO_MAX_H0) return XO_EINVAL;
+  if (ql < 0 || tl < 0 || ql > XO_MAX_LEN || tl > XO_MAX_LEN) return XO_EINVAL;
+  if (qo < 0 || to < 0) return XO_EINVAL;
+  if (qo > q_bytes - ql || to > t_bytes - tl) return XO_EINVAL;
+  return XO_OK;
+}
+
+typedef struct {
+  const uint8_t* q_seq; int64_t q_bytes; const int64_t* q_off; const int32_t* q_len;
+  const uint8_t* t_seq; int64_t t_bytes; const int64_t* t_off; const int32_t* t_len;
+  const int32_t* h0; int64_t n; const xo_scoring* sc; int32_t* out; int64_t* cells;
+  int64_t next; /* next unclaimed pair, taken in chunks */
+} batch_job;
+
+static void run_pair(batch_job* b, int64_t k) {
+  int32_t* o = b->out + 7 * k;
+  if (check_pair(b->q_off[k], b->q_len[k], b->q_bytes, b->t_off[k], b->t_len[k], b->t_bytes,
+                 b->h0[k]) != XO_OK) {
+    memset(o, 0, 7 * sizeof(int32_t));
+    o[6] = XO_EINVAL;
+    if (b->cells) b->cells[k] = 0;
+    return;
+  }
+  int64_t c = 0;
+  xo_extend_one(b->q_seq + b->q_off[k], b->q_len[k], b->t_seq + b->t_off[k], b->t_len[k],
+                b->h0[k], b->sc, o, &c, NULL, NULL, NULL, NULL, NULL, NULL);
+  if (b->cells) b->cells[k] = c;
+}
+
+static void* worker(void* arg) {
+  batch_job* b = (batch_job*)arg;
+  const int64_t chunk = 64;
+  for (;;) {
+    int64_t s = __atomic_fetch_add(&b->next, chunk, __ATOMIC_RELAXED);
+    if (s >= b->n) break;
+    int64_t e = s + chunk < b->n ? s + chunk : b->n;
+    for (int64_t k = s; k < e; ++k) run_pair(b, k);
+  }
+  return NULL;
+}
+
+/*
+ * Batch of independent pairs, spread over nthreads host threads (pairs are
+ * independent, so the split does not change any result).  Returns XO_EINVAL
+ * for an unacceptable scoring record (nothing is written), else XO_OK.
+ */
+int xo_extend_batch(const uint8_t* q_seq, int64_t q_bytes, const int64_t* q_off,
+                    const int32_t* q_len, const uint8_t* t_seq, int64_t t_bytes,
+                    const int64_t* t_off, const int32_t* t_len, const int32_t* h0, int64_t n,
+                    const xo_scoring* sc, int32_t* out, int64_t* cells, int nthreads) {
+  if (xo_check_scoring(sc) != XO_OK || n < 0) return XO_EINVAL;
+  batch_job b = {q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off, t_len, h0, n, sc, out,
+                 cells, 0};
+  if (nthreads < 1) nthreads = 1;
+  if (nthreads == 1) {
+    worker(&b);
+    return XO_OK;
+  }
+  pthread_t* th = malloc(sizeof(pthread_t) * (size_t)nthreads);
+  int started = 0;
+  for (int k = 0; k < nthreads; ++k)
+    if (pthread_create(&th[started], NULL, worker, &b) == 0) ++started;
+  if (started == 0) worker(&b);
+  for (int k = 0; k < started; ++k) pthread_join(th[k], NULL);
+  free(th);
+  return XO_OK;
+}

@@ -1,0 +1,90 @@
+"""The oracle's pins must catch plausible mistakes in the oracle itself.
+
+Each case plants one mistake in a copy of oracle/xt_oracle.c (on the CPU, in a
+temporary directory), loads the copy in place of the real oracle and checks
+that at least one pin check fails.
+"""
+import ctypes
+import os
+import random
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+import tests.test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "xt_oracle.c")
+
+MUTANTS = {
+    "local_restart": ("int64_t M = D > 0 ? D + score(sc, t[i], q[j]) : 0;",
+                      "int64_t M = D + score(sc, t[i], q[j]);"),
+    "gap_open_from_E_only": ("int64_t E = max2(0, max2(Hc[j] - alpha, Ec[j] - beta));",
+                             "int64_t E = max2(0, max2(Hc[j] - beta, Ec[j] - beta));"),
+    "F_wrong_extend": ("int64_t F = max2(0, max2(Hp[j + 1] - alpha, Fp[j + 1] - beta));",
+                       "int64_t F = max2(0, max2(Hp[j + 1] - alpha, Fp[j + 1] - alpha));"),
+    "diag_from_up": ("int64_t D = Hp[j];", "int64_t D = Hp[j + 1];"),
+    "band_off_by_one": ("return iabs64(r - c) <= w;", "return iabs64(r - c) < w;"),
+    "smallest_j_tie": ("if (H >= m) { m = H; mj = j; }", "if (H > m) { m = H; mj = j; }"),
+    "gscore_latest_row": ("if (g > 0 && g > gscore)", "if (g > 0 && g >= gscore)"),
+    "zdrop_no_gap_correction": ("int64_t drop = best - m - iabs64(d) * beta;",
+                                "int64_t drop = best - m;"),
+    "boundary_row_missing_open": ("int64_t v = max2(0, h0 - alpha - beta * c);",
+                                  "int64_t v = max2(0, h0 - beta - beta * c);"),
+    "n_scored_as_mismatch": ("if (a >= 4 || b >= 4) return sc->n_score;",
+                             "if (a >= 4 && b >= 4) return sc->n_score;"),
+    "transposed_score": ("score(sc, t[i], q[j])", "score(sc, t[j < tlen ? j : 0], q[i < qlen ? i : 0])"),
+    "max_off_signless": ("max_off = max2(max_off, iabs64(mj - i));",
+                         "max_off = max2(max_off, mj - i);"),
+    "cells_count_all_rows": ("for (int64_t i = 0; i <= last_live; ++i) n += band_width(i, qlen, w);",
+                             "for (int64_t i = 0; i < tlen; ++i) n += band_width(i, qlen, w);"),
+}
+
+
+def build_mutant(name, tmp):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert old in src, name
+    path = os.path.join(tmp, f"{name}.c")
+    with open(path, "w") as f:
+        f.write(src.replace(old, new))
+    so = os.path.join(tmp, f"lib{name}.so")
+    subprocess.run(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", "-pthread", path, "-o", so],
+                   check=True)
+    return so
+
+
+def pins_fail():
+    """Run the pin checks against whatever library oracle._LIB points at."""
+    checks = [
+        lambda: [pins.test_handworked_tables(n) for n in
+                 ("handworked_identical_3x3.json", "handworked_anchoring_3x3.json",
+                  "handworked_band_n_3x4.json")],
+        pins.test_handworked_zdrop_tail,
+        pins.test_single_deletion_closed_form,
+        pins.test_band_zero_is_diagonal_only,
+        pins.test_all_mismatch_single_cell_gscore,
+        pins.test_boundary_runs_match_enumeration,
+        pins.test_path_enumeration_fixes_every_cell,
+    ]
+    for c in checks:
+        try:
+            c()
+        except AssertionError:
+            return True
+    return False
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, monkeypatch):
+    with tempfile.TemporaryDirectory() as tmp:
+        so = build_mutant(name, tmp)
+        saved = oracle._LIB
+        try:
+            oracle._LIB = None
+            monkeypatch.setattr(oracle, "build", lambda force=False: so)
+            assert pins_fail(), f"no pin detects mutant {name}"
+        finally:
+            oracle._LIB = saved
