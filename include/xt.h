@@ -1,0 +1,174 @@
+/*
+ * xt.h -- batched seed extension on GB300 (sm_103a): the C ABI.
+ *
+ * Operation (arXiv 2301.09310, Sec. II-A, Eq. 1): for every pair, extend an
+ * exact-match seed of score h0 along a query q and a target (reference window)
+ * t with affine-gap dynamic programming.  Rows i index the target ("reference
+ * at i"), columns j the query ("query at j").  alpha = gap_open + gap_extend
+ * is the cost of a gap's first base and beta = gap_extend of each further
+ * base (Eq. 1's alpha and beta).  The DP runs on an extended matrix with a
+ * seed cell H(-1,-1) = h0, a boundary row and column of pure gap runs from the
+ * seed, a static band |i - j| <= w (cells outside it are dead), and the
+ * anchoring rule that a cell of value 0 is dead and is not restarted by a
+ * later match (extension stays tied to its seed).  After each target row, in
+ * row order, the row maximum m_i (largest column on ties) updates the local
+ * best; a row that does not improve it stops the extension when
+ *   best - m_i - |(i - bi) - (mj_i - bj)| * beta > zdrop      (zdrop > 0).
+ * The end-to-end score is the best H at the last query column (earliest row
+ * on ties).  The paper states only plain Eq. 1; the seed, band and z-drop
+ * reading above is this library's, and every result is bit-exact against the
+ * scalar CPU oracle that implements it.
+ *
+ * Conventions of every entry point:
+ *   - Sequences are uint8 base codes: 0,1,2,3 = A,C,G,T; any value >= 4 is N.
+ *     Pairs are concatenated: pair k's query is q_seq[q_off[k] .. q_off[k] +
+ *     q_len[k]), its target t_seq[t_off[k] .. t_off[k] + t_len[k]).
+ *   - Pointers marked "device" must be device memory (cudaMalloc, torch CUDA
+ *     tensors) of the context's device; the caller owns them and the library
+ *     never frees them.  Work is enqueued on `stream` (a cudaStream_t; NULL is
+ *     the legacy default stream) and is asynchronous: results are valid after
+ *     the stream has been synchronised.  Inputs must stay alive and unchanged
+ *     until then.
+ *   - Argument and scoring errors are reported synchronously, before anything
+ *     is enqueued (XT_EINVAL).  Per-pair input errors (h0 < 1 or > XT_MAX_H0,
+ *     negative or too long lengths, a sequence outside its buffer) set that
+ *     pair's status to XT_EINVAL, zero its other fields and cells, and leave
+ *     the other pairs unaffected.  Device errors surface as XT_ECUDA at the
+ *     call or at xt_ctx_sync.  No call aborts the process or traps the GPU.
+ *   - Pairs are independent: a pair's result does not depend on the other
+ *     pairs of the batch, the schedule or the kernel that computed it.
+ */
+#ifndef XT_H
+#define XT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define XT_ABI_VERSION 1
+#define XT_MAX_LEN (1 << 20)  /* longest accepted query or target (bases) */
+#define XT_MAX_H0 (1 << 20)   /* largest accepted seed score */
+
+typedef enum {
+  XT_OK = 0,
+  XT_EINVAL = 1,   /* bad argument, scoring record or pair */
+  XT_ENOMEM = 2,   /* the context's memory budget or the device is exhausted */
+  XT_ECUDA = 3,    /* a CUDA call or kernel failed */
+  XT_ETIMEOUT = 4, /* a bounded device-side wait expired */
+  XT_EBUSY = 5     /* resource in use (e.g. serving queue full) */
+} xt_status;
+
+/*
+ * Scoring record (Eq. 1's S, alpha, beta; band and z-drop of seed extension).
+ *   match      in [1, 127]     score of two equal bases A/C/G/T
+ *   mismatch   in [-127, 0]    score of two different bases (signed)
+ *   gap_open   in [0, 1023]    a gap of k bases costs gap_open + k * gap_extend
+ *   gap_extend in [0, 1023]
+ *   w          >= 0            band: cell (i, j) exists iff |i - j| <= w
+ *   zdrop      any             <= 0 disables the z-drop cutoff
+ *   n_score    in [-127, 0]    score of any pair of bases involving N
+ */
+typedef struct {
+  int32_t match, mismatch, gap_open, gap_extend, w, zdrop, n_score;
+} xt_scoring;
+
+/*
+ * Result of one extension, 7 x int32 = 28 bytes, in input order.
+ *   score    local best (>= h0)               qle  query bases consumed at it
+ *   tle      target bases consumed at it      gscore end-to-end score at the
+ *            last query column, -1 if never reached with a live cell
+ *   gtle     target bases consumed at gscore  max_off  largest |j - i| of the
+ *            rows that raised the best        status   XT_OK or XT_EINVAL
+ * qlen == 0 gives {h0,0,0,h0,0,0,OK}; tlen == 0 gives {h0,0,0,-1,0,0,OK}.
+ */
+typedef struct {
+  int32_t score, qle, tle, gscore, gtle, max_off, status;
+} xt_result;
+
+typedef struct xt_ctx xt_ctx;
+
+/*
+ * Create a context on CUDA device `device` (made current for the call).
+ * mem_budget_bytes caps the device workspace the context may hold (0 = no
+ * cap beyond the device).  *ctx receives the handle; XT_EINVAL on a NULL ctx
+ * or a bad device, XT_ECUDA when the device cannot be used.
+ */
+xt_status xt_ctx_create(xt_ctx** ctx, int device, size_t mem_budget_bytes);
+
+/* Release the context and its workspace (after synchronising its work). */
+xt_status xt_ctx_destroy(xt_ctx* ctx);
+
+/* Wait for the context's work on `stream`; reports pending device errors. */
+xt_status xt_ctx_sync(xt_ctx* ctx, void* stream);
+
+/*
+ * Batched extension (the fast path).  A classify pass validates each pair
+ * and sorts the batch into length buckets; persistent kernels then pull pairs
+ * from device-side queues, each bucket with its own schedule (pairs per warp,
+ * rows per lane, packed 16-bit or 32-bit arithmetic where a per-pair score
+ * bound makes it exact).
+ *
+ *   q_seq, t_seq       device, uint8 codes; q_bytes / t_bytes their sizes
+ *   q_off, t_off       device, int64[n_pairs]
+ *   q_len, t_len, h0   device, int32[n_pairs]
+ *   n_pairs            >= 0
+ *   sc                 host pointer to the scoring record (read during the call)
+ *   out                device, xt_result[n_pairs]
+ *   cells_out          device int64[n_pairs] or NULL: useful in-band cells of
+ *                      each pair (rows 0 .. the last live row not after the
+ *                      z-drop stop row, summed over their band widths)
+ *   stream             cudaStream_t
+ * Device workspace comes from the context (grown as needed within its budget;
+ * XT_ENOMEM if it cannot).
+ */
+xt_status xt_extend_batch(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_bytes,
+                          const int64_t* q_off, const int32_t* q_len, const uint8_t* t_seq,
+                          int64_t t_bytes, const int64_t* t_off, const int32_t* t_len,
+                          const int32_t* h0, int32_t n_pairs, const xt_scoring* sc,
+                          xt_result* out, int64_t* cells_out, void* stream);
+
+/*
+ * Plain extension: one pair per thread block (one warp), 32-bit arithmetic,
+ * no bucketing and no persistent queue -- the comparison kernel.  Same
+ * arguments, conventions and results as xt_extend_batch.
+ */
+xt_status xt_extend_batch_plain(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_bytes,
+                                const int64_t* q_off, const int32_t* q_len, const uint8_t* t_seq,
+                                int64_t t_bytes, const int64_t* t_off, const int32_t* t_len,
+                                const int32_t* h0, int32_t n_pairs, const xt_scoring* sc,
+                                xt_result* out, int64_t* cells_out, void* stream);
+
+/*
+ * End-to-end variant of xt_extend_batch on HOST buffers (same argument
+ * meaning, every pointer a host pointer; pinned memory is fastest).  Copies
+ * the inputs to the device, extends, copies results (and cells when
+ * cells_out != NULL) back, and returns after the stream has synchronised.
+ */
+xt_status xt_extend_batch_host(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_bytes,
+                               const int64_t* q_off, const int32_t* q_len, const uint8_t* t_seq,
+                               int64_t t_bytes, const int64_t* t_off, const int32_t* t_len,
+                               const int32_t* h0, int32_t n_pairs, const xt_scoring* sc,
+                               xt_result* out, int64_t* cells_out, void* stream);
+
+/*
+ * Override the schedule of the batched path (testing and tuning aid).  P lanes
+ * per pair (1, 2, 4, 8, 16 or 32) and R target rows per lane (4, 8, or 16 with
+ * P <= 4) then apply to every length bucket whose ring still fits in shared
+ * memory; P = 0 restores the built-in per-bucket table.  Results never depend
+ * on the schedule.  XT_EINVAL for an unsupported (P, R).
+ */
+xt_status xt_ctx_set_schedule(xt_ctx* ctx, int P, int R);
+
+/* Human-readable name of a status code (static storage). */
+const char* xt_status_str(xt_status s);
+
+/* Last error message recorded by the context (static per context; "" if none). */
+const char* xt_ctx_last_error(const xt_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* XT_H */

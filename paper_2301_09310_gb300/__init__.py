@@ -1,0 +1,257 @@
+"""Batched seed extension on GB300: Python binding of the libxt C ABI.
+
+Argument marshalling only.  Every step of the extension runs in the CUDA
+kernels of libxt (csrc/); there is no CPU implementation here and no
+fallback: if the library is not built or no GPU is present, calls raise.
+The functions carry the C names of include/xt.h (xt_ctx_create,
+xt_extend_batch, ...); ``Context`` is a small convenience wrapper over them
+taking torch CUDA tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+from . import build as _build
+
+XT_OK, XT_EINVAL, XT_ENOMEM, XT_ECUDA, XT_ETIMEOUT, XT_EBUSY = range(6)
+XT_MAX_LEN = 1 << 20
+XT_MAX_H0 = 1 << 20
+RESULT_FIELDS = ("score", "qle", "tle", "gscore", "gtle", "max_off", "status")
+
+EXPORTED = ("xt_ctx_create", "xt_ctx_destroy", "xt_ctx_sync", "xt_extend_batch",
+            "xt_extend_batch_plain", "xt_extend_batch_host", "xt_status_str",
+            "xt_ctx_last_error", "xt_ctx_set_schedule")
+
+
+class xt_scoring(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in
+                ("match", "mismatch", "gap_open", "gap_extend", "w", "zdrop", "n_score")]
+
+
+class XtError(RuntimeError):
+    def __init__(self, status: int, msg: str = ""):
+        self.status = status
+        super().__init__(f"{_status_name(status)}: {msg}" if msg else _status_name(status))
+
+
+_LIB = None
+
+
+def _status_name(s: int) -> str:
+    names = ["XT_OK", "XT_EINVAL", "XT_ENOMEM", "XT_ECUDA", "XT_ETIMEOUT", "XT_EBUSY"]
+    return names[s] if 0 <= s < len(names) else f"XT_STATUS_{s}"
+
+
+def lib_path() -> str:
+    return _build.lib_path()
+
+
+def load_library(path: str | None = None):
+    """Load libxt (built by build.build()); raises if it is missing."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libxt is not built ({path} missing): run "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    batch_args = [P, P, I64, P, P, P, I64, P, P, P, I32, ctypes.POINTER(xt_scoring), P, P, P]
+    lib.xt_ctx_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.c_size_t]
+    lib.xt_ctx_destroy.argtypes = [P]
+    lib.xt_ctx_sync.argtypes = [P, P]
+    for fn in ("xt_extend_batch", "xt_extend_batch_plain", "xt_extend_batch_host"):
+        getattr(lib, fn).argtypes = batch_args
+    for fn in ("xt_ctx_create", "xt_ctx_destroy", "xt_ctx_sync", "xt_extend_batch",
+               "xt_extend_batch_plain", "xt_extend_batch_host"):
+        getattr(lib, fn).restype = ctypes.c_int
+    lib.xt_status_str.argtypes = [ctypes.c_int]
+    lib.xt_status_str.restype = ctypes.c_char_p
+    lib.xt_ctx_set_schedule.argtypes = [P, ctypes.c_int, ctypes.c_int]
+    lib.xt_ctx_set_schedule.restype = ctypes.c_int
+    lib.xt_ctx_last_error.argtypes = [P]
+    lib.xt_ctx_last_error.restype = ctypes.c_char_p
+    _LIB = lib
+    return lib
+
+
+# ------------------------------------------------------------ C-ABI mirrors
+def xt_ctx_create(device: int = 0, mem_budget_bytes: int = 0) -> int:
+    h = ctypes.c_void_p()
+    s = load_library().xt_ctx_create(ctypes.byref(h), int(device), int(mem_budget_bytes))
+    if s != XT_OK:
+        raise XtError(s, "xt_ctx_create")
+    return h.value
+
+
+def xt_ctx_destroy(ctx: int) -> int:
+    return load_library().xt_ctx_destroy(ctypes.c_void_p(ctx))
+
+
+def xt_ctx_sync(ctx: int, stream: int = 0) -> int:
+    return load_library().xt_ctx_sync(ctypes.c_void_p(ctx), ctypes.c_void_p(stream))
+
+
+def xt_ctx_set_schedule(ctx: int, P: int, R: int) -> int:
+    return load_library().xt_ctx_set_schedule(ctypes.c_void_p(ctx), int(P), int(R))
+
+
+def xt_status_str(s: int) -> str:
+    return load_library().xt_status_str(int(s)).decode()
+
+
+def xt_ctx_last_error(ctx: int) -> str:
+    return load_library().xt_ctx_last_error(ctypes.c_void_p(ctx)).decode()
+
+
+def _call(fn: str, ctx, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off, t_len, h0, n,
+          sc: xt_scoring, out, cells, stream) -> int:
+    f = getattr(load_library(), fn)
+    return f(ctypes.c_void_p(ctx), ctypes.c_void_p(q_seq), int(q_bytes), ctypes.c_void_p(q_off),
+             ctypes.c_void_p(q_len), ctypes.c_void_p(t_seq), int(t_bytes), ctypes.c_void_p(t_off),
+             ctypes.c_void_p(t_len), ctypes.c_void_p(h0), int(n), ctypes.byref(sc),
+             ctypes.c_void_p(out), ctypes.c_void_p(cells), ctypes.c_void_p(stream))
+
+
+def xt_extend_batch(ctx, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off, t_len, h0, n, sc,
+                    out, cells, stream) -> int:
+    """Raw pointers (ints) as in include/xt.h; returns the xt_status."""
+    return _call("xt_extend_batch", ctx, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off,
+                 t_len, h0, n, sc, out, cells, stream)
+
+
+def xt_extend_batch_plain(ctx, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off, t_len, h0, n,
+                          sc, out, cells, stream) -> int:
+    return _call("xt_extend_batch_plain", ctx, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off,
+                 t_len, h0, n, sc, out, cells, stream)
+
+
+def xt_extend_batch_host(ctx, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off, t_len, h0, n,
+                         sc, out, cells, stream) -> int:
+    return _call("xt_extend_batch_host", ctx, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off,
+                 t_len, h0, n, sc, out, cells, stream)
+
+
+# ------------------------------------------------------------ convenience
+@dataclass(frozen=True)
+class Scoring:
+    match: int = 1
+    mismatch: int = -4
+    gap_open: int = 6
+    gap_extend: int = 1
+    w: int = 100
+    zdrop: int = 100
+    n_score: int = -1
+
+    def c(self) -> xt_scoring:
+        return xt_scoring(self.match, self.mismatch, self.gap_open, self.gap_extend, self.w,
+                          self.zdrop, self.n_score)
+
+
+def _scoring(sc) -> xt_scoring:
+    if isinstance(sc, xt_scoring):
+        return sc
+    if hasattr(sc, "as_tuple"):
+        return xt_scoring(*sc.as_tuple())
+    if hasattr(sc, "c"):
+        return sc.c()
+    return xt_scoring(*sc)
+
+
+class Context:
+    """A libxt context on one CUDA device, taking torch tensors.
+
+    Inputs are CUDA tensors (uint8 sequences, int64 offsets, int32 lengths and
+    h0); results come back as an int32 [n, 7] CUDA tensor (RESULT_FIELDS) and
+    an int64 [n] tensor of useful cells.  Work is enqueued on the current torch
+    stream unless a stream is given."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0):
+        import torch  # noqa: F401  (device memory and streams)
+        self.device = int(device)
+        self.handle = xt_ctx_create(self.device, mem_budget_bytes)
+
+    def close(self):
+        if self.handle:
+            xt_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_schedule(self, P: int = 0, R: int = 8):
+        self._check(xt_ctx_set_schedule(self.handle, P, R), "xt_ctx_set_schedule")
+
+    def _check(self, s: int, what: str):
+        if s != XT_OK:
+            raise XtError(s, f"{what}: {xt_ctx_last_error(self.handle)}")
+
+    @staticmethod
+    def _dev(t, dtype, name):
+        import torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda):
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if t.dtype != dtype:
+            raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        return t
+
+    def extend(self, q_seq, q_off, q_len, t_seq, t_off, t_len, h0, scoring, plain=False,
+               out=None, cells=None, want_cells=True, stream=None):
+        import torch
+        d = self._dev
+        q_seq = d(q_seq, torch.uint8, "q_seq")
+        t_seq = d(t_seq, torch.uint8, "t_seq")
+        q_off = d(q_off, torch.int64, "q_off")
+        t_off = d(t_off, torch.int64, "t_off")
+        q_len = d(q_len, torch.int32, "q_len")
+        t_len = d(t_len, torch.int32, "t_len")
+        h0 = d(h0, torch.int32, "h0")
+        n = int(q_len.numel())
+        for name, t in (("q_off", q_off), ("t_off", t_off), ("t_len", t_len), ("h0", h0)):
+            if t.numel() != n:
+                raise ValueError(f"{name} has {t.numel()} entries, expected {n}")
+        dev = q_len.device
+        if out is None:
+            out = torch.empty((n, 7), dtype=torch.int32, device=dev)
+        if cells is None and want_cells:
+            cells = torch.empty(n, dtype=torch.int64, device=dev)
+        if stream is None:
+            stream = torch.cuda.current_stream(dev)
+        fn = "xt_extend_batch_plain" if plain else "xt_extend_batch"
+        s = _call(fn, self.handle, q_seq.data_ptr(), q_seq.numel(), q_off.data_ptr(),
+                  q_len.data_ptr(), t_seq.data_ptr(), t_seq.numel(), t_off.data_ptr(),
+                  t_len.data_ptr(), h0.data_ptr(), n, _scoring(scoring), out.data_ptr(),
+                  cells.data_ptr() if cells is not None else 0, stream.cuda_stream)
+        self._check(s, fn)
+        return out, cells
+
+    def extend_host(self, q_seq, q_off, q_len, t_seq, t_off, t_len, h0, scoring, out=None,
+                    cells=None, stream=None):
+        """Host (numpy, ideally pinned) buffers in and out; returns after completion."""
+        import numpy as np
+        import torch
+        arrs = [np.ascontiguousarray(a, dt) for a, dt in
+                ((q_seq, np.uint8), (q_off, np.int64), (q_len, np.int32), (t_seq, np.uint8),
+                 (t_off, np.int64), (t_len, np.int32), (h0, np.int32))]
+        q_seq, q_off, q_len, t_seq, t_off, t_len, h0 = arrs
+        n = int(q_len.size)
+        if out is None:
+            out = np.empty((n, 7), np.int32)
+        if cells is None:
+            cells = np.empty(n, np.int64)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        p = lambda a: a.ctypes.data  # noqa: E731
+        s = _call("xt_extend_batch_host", self.handle, p(q_seq), q_seq.size, p(q_off), p(q_len),
+                  p(t_seq), t_seq.size, p(t_off), p(t_len), p(h0), n, _scoring(scoring), p(out),
+                  p(cells), stream.cuda_stream)
+        self._check(s, "xt_extend_batch_host")
+        return out, cells

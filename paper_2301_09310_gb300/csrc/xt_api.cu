@@ -1,0 +1,445 @@
+// xt_api.cu -- the C ABI of include/xt.h: context, argument checks, device
+// workspace, launch plan and the host-buffer (end-to-end) variant.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "xt.h"
+#include "xt_kernels.cuh"
+
+using namespace xt;
+
+struct xt_ctx {
+  int device = 0;
+  int num_sms = 0;
+  int smem_optin = 0;
+  size_t budget = 0;            // 0: no cap
+  size_t held = 0;              // bytes of device memory held
+  // per-call workspace (grown on demand)
+  void* work = nullptr;
+  size_t work_bytes = 0;
+  // global ring pool for pairs whose band does not fit in shared memory
+  int2* pool = nullptr;
+  size_t pool_bytes = 0;
+  // end-to-end staging: device copies of host inputs and pinned host mirrors
+  void* dev_in = nullptr;
+  size_t dev_in_bytes = 0;
+  int forced_P = 0;              // schedule override (0: per-bucket table)
+  int forced_R = 0;
+  std::mutex mu;
+  std::string last_error;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kPlainRsCapLog2 = 13;    // plain kernel ring up to 8192 entries (64 KB)
+constexpr int kQueueRsCapLog2 = 12;    // queue kernels: ring up to 4096 entries per group
+constexpr size_t kPoolCap = 512u << 20;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+int log2_ceil(int64_t x) {
+  int k = 0;
+  while (((int64_t)1 << k) < x) ++k;
+  return k;
+}
+
+xt_status fail(xt_ctx* ctx, xt_status s, const std::string& msg) {
+  if (ctx) ctx->last_error = msg;
+  return s;
+}
+
+xt_status cuda_fail(xt_ctx* ctx, cudaError_t e, const char* where) {
+  return fail(ctx, XT_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bool scoring_ok(const xt_scoring* sc) {
+  if (!sc) return false;
+  if (sc->match < 1 || sc->match > 127) return false;
+  if (sc->mismatch > 0 || sc->mismatch < -127) return false;
+  if (sc->n_score > 0 || sc->n_score < -127) return false;
+  if (sc->gap_open < 0 || sc->gap_open > 1023) return false;
+  if (sc->gap_extend < 0 || sc->gap_extend > 1023) return false;
+  if (sc->w < 0) return false;
+  return true;
+}
+
+Score make_score(const xt_scoring* s) {
+  Score sc;
+  sc.alpha = s->gap_open + s->gap_extend;
+  sc.beta = s->gap_extend;
+  // a band wider than any pair changes nothing; clamp so index arithmetic stays in int32
+  sc.w = s->w > 2 * XT_MAX_LEN ? 2 * XT_MAX_LEN : s->w;
+  sc.zdrop = s->zdrop;
+  const uint32_t mb = (uint8_t)(int8_t)s->match, xb = (uint8_t)(int8_t)s->mismatch,
+                 nb = (uint8_t)(int8_t)s->n_score;
+  for (int qc = 0; qc < 4; ++qc) {
+    uint32_t v = 0;
+    for (int tb = 0; tb < 4; ++tb) v |= (tb == qc ? mb : xb) << (8 * tb);
+    sc.prof[qc] = v;
+  }
+  sc.nnnn = nb | (nb << 8) | (nb << 16) | (nb << 24);
+  sc.prof[4] = sc.nnnn;
+  return sc;
+}
+
+xt_status dev_alloc(xt_ctx* ctx, void** p, size_t* have, size_t want) {
+  if (*have >= want) return XT_OK;
+  const size_t grow = want - *have;
+  if (ctx->budget && ctx->held + grow > ctx->budget)
+    return fail(ctx, XT_ENOMEM, "device memory budget exceeded");
+  if (*p) {
+    cudaFree(*p);
+    ctx->held -= *have;
+    *p = nullptr;
+    *have = 0;
+  }
+  cudaError_t e = cudaMalloc(p, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(ctx, XT_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  *have = want;
+  ctx->held += want;
+  return XT_OK;
+}
+
+// Carve the per-call workspace for n pairs.
+xt_status get_work(xt_ctx* ctx, int32_t n, Work* w) {
+  size_t off = 0;
+  const size_t o_pclass = off; off = align_up(off + (size_t)n);
+  const size_t o_order = off; off = align_up(off + 4 * (size_t)n);
+  const size_t o_counts = off; off = align_up(off + 4 * (size_t)kNumBuckets);
+  const size_t o_cursor = off; off = align_up(off + 4 * (size_t)kNumBuckets);
+  const size_t o_sb = off; off = align_up(off + 4 * (size_t)(kNumClasses * kNumJ));
+  const size_t o_se = off; off = align_up(off + 4 * (size_t)(kNumClasses * kNumJ));
+  const size_t o_heads = off; off = align_up(off + 4 * (size_t)kMaxLaunches);
+  const size_t o_huge = off; off = align_up(off + (size_t)kNumJ);
+  xt_status s = dev_alloc(ctx, &ctx->work, &ctx->work_bytes, off);
+  if (s != XT_OK) return s;
+  char* base = (char*)ctx->work;
+  w->pclass = (uint8_t*)(base + o_pclass);
+  w->order = (int32_t*)(base + o_order);
+  w->counts = (int32_t*)(base + o_counts);
+  w->cursor = (int32_t*)(base + o_cursor);
+  w->seg_begin = (int32_t*)(base + o_sb);
+  w->seg_end = (int32_t*)(base + o_se);
+  w->heads = (int32_t*)(base + o_heads);
+  w->huge_j = (uint8_t*)(base + o_huge);
+  return XT_OK;
+}
+
+struct Plan {
+  Launch launch[kMaxLaunches];
+  int n_launch = 0;
+  uint8_t huge_j[kNumJ] = {0};
+  bool any_huge = false;
+  int64_t slab = 0;
+};
+
+int64_t next_pow2(int64_t x) { return (int64_t)1 << log2_ceil(x); }
+
+// Schedule of bucket j (queries of qlen + 2 <= 2^j): the fewest lanes per pair
+// whose shared-memory ring fits 32 KB per CTA.  The ring needs
+// min(qlen, P*R + 2w) + 2 entries.
+void bucket_schedule(const xt_ctx* ctx, int j, int w, int* P, int* R, int* rs_log2, bool* huge) {
+  if (ctx->forced_P) {
+    const int64_t need = std::min<int64_t>(
+        (int64_t)1 << j, next_pow2((int64_t)ctx->forced_P * ctx->forced_R + 2 * (int64_t)w + 2));
+    const int lg = log2_ceil(need);
+    if (lg <= kQueueRsCapLog2 &&
+        queue_smem_bytes(ctx->forced_P, lg) <= (size_t)ctx->smem_optin - 1024) {
+      *P = ctx->forced_P; *R = ctx->forced_R; *rs_log2 = lg; *huge = false;
+      return;
+    }
+  }
+  const int Rr = 8;
+  for (int p = 1; p <= 32; p *= 2) {
+    const int64_t need = std::min<int64_t>((int64_t)1 << j, next_pow2((int64_t)p * Rr + 2 * (int64_t)w + 2));
+    const int lg = log2_ceil(need);
+    const size_t bytes = queue_smem_bytes(p, lg);
+    if (bytes <= 32 * 1024 || (p == 32 && lg <= kQueueRsCapLog2)) {
+      *P = p; *R = Rr; *rs_log2 = lg; *huge = false;
+      return;
+    }
+  }
+  *P = 32; *R = 8; *rs_log2 = 0; *huge = true;
+}
+
+void add_huge_launch(xt_ctx* ctx, const Score& sc, Plan* pl) {
+  // global slabs: ring of min(qlen, 256 + 2w) + 2 entries, qlen <= XT_MAX_LEN
+  const int64_t need = std::min<int64_t>(XT_MAX_LEN, 256 + 2 * (int64_t)sc.w) + 2;
+  pl->slab = next_pow2(need);
+  const int64_t per_cta = (kQueueThreads / 32) * pl->slab * (int64_t)sizeof(int2);
+  int64_t grid = (int64_t)kPoolCap / per_cta;
+  if (grid > 2 * ctx->num_sms) grid = 2 * ctx->num_sms;
+  if (grid < 1) grid = 1;
+  Launch& L = pl->launch[pl->n_launch++];
+  L.cls = CLS_HUGE; L.j_lo = 0; L.j_hi = kJMax; L.P = 32; L.R = 8; L.rs_log2 = 0;
+  L.global_ring = true; L.slab = pl->slab; L.grid = (int)grid;
+}
+
+void plan_batched(xt_ctx* ctx, const Score& sc, Plan* pl) {
+  for (int cls = CLS_NARROW; cls <= CLS_WIDE; ++cls) {
+    int prev = -1;
+    for (int j = kJMax; j >= kJMin; --j) {
+      int P, R, lg;
+      bool huge;
+      bucket_schedule(ctx, j, sc.w, &P, &R, &lg, &huge);
+      if (huge) {
+        pl->huge_j[j] = 1;
+        pl->any_huge = true;
+        prev = -1;
+        continue;
+      }
+      if (prev >= 0) {
+        Launch& L = pl->launch[prev];
+        if (L.P == P && L.R == R && L.rs_log2 == lg) {
+          L.j_lo = j;
+          continue;
+        }
+      }
+      Launch& L = pl->launch[pl->n_launch];
+      L.cls = cls; L.j_lo = j; L.j_hi = (j == kJMax ? kJMax : j); L.P = P; L.R = R;
+      L.rs_log2 = lg; L.global_ring = false; L.slab = 0;
+      const size_t smem = queue_smem_bytes(P, lg);
+      int per_sm = (int)std::min<size_t>(16, std::max<size_t>(1, (size_t)(220 * 1024) / std::max<size_t>(smem + 1024, 1)));
+      L.grid = ctx->num_sms * per_sm;
+      prev = pl->n_launch++;
+    }
+    // the lowest bucket also takes the pairs below kJMin (classify clamps j)
+    if (prev >= 0) pl->launch[prev].j_lo = 0;
+  }
+  if (pl->any_huge) add_huge_launch(ctx, sc, pl);
+}
+
+void plan_plain(xt_ctx* ctx, const Score& sc, Plan* pl, int* rs_log2) {
+  const int64_t need = 256 + 2 * (int64_t)sc.w + 2;
+  int lg = log2_ceil(need);
+  if (lg > kPlainRsCapLog2) lg = kPlainRsCapLog2;
+  *rs_log2 = lg;
+  for (int j = kJMin; j <= kJMax; ++j) {
+    // a pair of bucket j needs at most min(2^j, 256 + 2w + 2) ring entries
+    const int64_t nj = std::min<int64_t>((int64_t)1 << j, next_pow2(need));
+    if (nj > ((int64_t)1 << lg)) {
+      pl->huge_j[j] = 1;
+      pl->any_huge = true;
+    }
+  }
+  if (pl->any_huge) add_huge_launch(ctx, sc, pl);
+}
+
+xt_status check_args(xt_ctx* ctx, const void* q_seq, int64_t q_bytes, const void* q_off,
+                     const void* q_len, const void* t_seq, int64_t t_bytes, const void* t_off,
+                     const void* t_len, const void* h0, int32_t n, const xt_scoring* sc,
+                     const void* out) {
+  if (!ctx) return XT_EINVAL;
+  if (n < 0) return fail(ctx, XT_EINVAL, "n_pairs < 0");
+  if (!scoring_ok(sc)) return fail(ctx, XT_EINVAL, "scoring record out of range");
+  if (q_bytes < 0 || t_bytes < 0) return fail(ctx, XT_EINVAL, "negative buffer size");
+  if (n > 0 && (!q_off || !q_len || !t_off || !t_len || !h0 || !out))
+    return fail(ctx, XT_EINVAL, "null array");
+  if ((q_bytes > 0 && !q_seq) || (t_bytes > 0 && !t_seq))
+    return fail(ctx, XT_EINVAL, "null sequence buffer");
+  return XT_OK;
+}
+
+xt_status run(xt_ctx* ctx, bool plain, const uint8_t* q_seq, int64_t q_bytes, const int64_t* q_off,
+              const int32_t* q_len, const uint8_t* t_seq, int64_t t_bytes, const int64_t* t_off,
+              const int32_t* t_len, const int32_t* h0, int32_t n, const xt_scoring* scr,
+              xt_result* out, int64_t* cells, cudaStream_t stream) {
+  xt_status s = check_args(ctx, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off, t_len, h0, n,
+                           scr, out);
+  if (s != XT_OK) return s;
+  if (n == 0) return XT_OK;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+  const Score sc = make_score(scr);
+  Work w;
+  s = get_work(ctx, n, &w);
+  if (s != XT_OK) return s;
+  Plan pl;
+  int plain_rs = 0;
+  if (plain) plan_plain(ctx, sc, &pl, &plain_rs);
+  else plan_batched(ctx, sc, &pl);
+  if (pl.any_huge) {
+    const size_t want = (size_t)pl.launch[pl.n_launch - 1].grid * (kQueueThreads / 32) *
+                        (size_t)pl.slab * sizeof(int2);
+    s = dev_alloc(ctx, (void**)&ctx->pool, &ctx->pool_bytes, want);
+    if (s != XT_OK) return s;
+  }
+  Batch b;
+  b.q_seq = q_seq; b.t_seq = t_seq; b.q_off = q_off; b.t_off = t_off; b.q_len = q_len;
+  b.t_len = t_len; b.h0 = h0; b.q_bytes = q_bytes; b.t_bytes = t_bytes; b.n = n; b.out = out;
+  b.cells = cells;
+  // small control block: counts, heads and the bucket flags
+  e = cudaMemsetAsync(w.counts, 0, 4 * (size_t)kNumBuckets, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.heads, 0, 4 * (size_t)kMaxLaunches, stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(w.huge_j, pl.huge_j, kNumJ, cudaMemcpyHostToDevice, stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "workspace init");
+  e = launch_classify(b, sc, scr->match, w, stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "classify");
+  e = launch_order(b, w, stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "order");
+  if (plain) {
+    e = launch_plain(b, sc, w, plain_rs, stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plain kernel");
+  }
+  for (int i = 0; i < pl.n_launch; ++i) {
+    e = launch_queue(b, sc, w, pl.launch[i], i, ctx->pool, stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "queue kernel");
+  }
+  return XT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+xt_status xt_ctx_create(xt_ctx** out, int device, size_t mem_budget_bytes) {
+  if (!out) return XT_EINVAL;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return XT_EINVAL;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return XT_ECUDA;
+  xt_ctx* c = new xt_ctx();
+  c->device = device;
+  c->budget = mem_budget_bytes;
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  c->smem_optin = max_smem_per_block_optin(device);
+  *out = c;
+  return XT_OK;
+}
+
+xt_status xt_ctx_destroy(xt_ctx* ctx) {
+  if (!ctx) return XT_EINVAL;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->work) cudaFree(ctx->work);
+  if (ctx->pool) cudaFree(ctx->pool);
+  if (ctx->dev_in) cudaFree(ctx->dev_in);
+  delete ctx;
+  return XT_OK;
+}
+
+xt_status xt_ctx_sync(xt_ctx* ctx, void* stream) {
+  if (!ctx) return XT_EINVAL;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+  return XT_OK;
+}
+
+xt_status xt_extend_batch(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_bytes,
+                          const int64_t* q_off, const int32_t* q_len, const uint8_t* t_seq,
+                          int64_t t_bytes, const int64_t* t_off, const int32_t* t_len,
+                          const int32_t* h0, int32_t n_pairs, const xt_scoring* sc,
+                          xt_result* out, int64_t* cells_out, void* stream) {
+  if (!ctx) return XT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  return run(ctx, false, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off, t_len, h0, n_pairs,
+             sc, out, cells_out, (cudaStream_t)stream);
+}
+
+xt_status xt_extend_batch_plain(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_bytes,
+                                const int64_t* q_off, const int32_t* q_len, const uint8_t* t_seq,
+                                int64_t t_bytes, const int64_t* t_off, const int32_t* t_len,
+                                const int32_t* h0, int32_t n_pairs, const xt_scoring* sc,
+                                xt_result* out, int64_t* cells_out, void* stream) {
+  if (!ctx) return XT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  return run(ctx, true, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off, t_len, h0, n_pairs,
+             sc, out, cells_out, (cudaStream_t)stream);
+}
+
+xt_status xt_extend_batch_host(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_bytes,
+                               const int64_t* q_off, const int32_t* q_len, const uint8_t* t_seq,
+                               int64_t t_bytes, const int64_t* t_off, const int32_t* t_len,
+                               const int32_t* h0, int32_t n_pairs, const xt_scoring* sc,
+                               xt_result* out, int64_t* cells_out, void* stream) {
+  if (!ctx) return XT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  xt_status s = check_args(ctx, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off, t_len, h0,
+                           n_pairs, sc, out);
+  if (s != XT_OK) return s;
+  if (n_pairs == 0) return XT_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, XT_ECUDA, "cudaSetDevice");
+  const size_t n = (size_t)n_pairs;
+  size_t off = 0;
+  const size_t o_q = off; off = align_up(off + (size_t)q_bytes);
+  const size_t o_t = off; off = align_up(off + (size_t)t_bytes);
+  const size_t o_qo = off; off = align_up(off + 8 * n);
+  const size_t o_to = off; off = align_up(off + 8 * n);
+  const size_t o_ql = off; off = align_up(off + 4 * n);
+  const size_t o_tl = off; off = align_up(off + 4 * n);
+  const size_t o_h0 = off; off = align_up(off + 4 * n);
+  const size_t o_out = off; off = align_up(off + sizeof(xt_result) * n);
+  const size_t o_cells = off; off = align_up(off + 8 * n);
+  s = dev_alloc(ctx, &ctx->dev_in, &ctx->dev_in_bytes, off);
+  if (s != XT_OK) return s;
+  char* d = (char*)ctx->dev_in;
+  cudaError_t e = cudaSuccess;
+  auto h2d = [&](size_t o, const void* src, size_t bytes) {
+    if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(d + o, src, bytes, cudaMemcpyHostToDevice, st);
+  };
+  h2d(o_q, q_seq, (size_t)q_bytes);
+  h2d(o_t, t_seq, (size_t)t_bytes);
+  h2d(o_qo, q_off, 8 * n);
+  h2d(o_to, t_off, 8 * n);
+  h2d(o_ql, q_len, 4 * n);
+  h2d(o_tl, t_len, 4 * n);
+  h2d(o_h0, h0, 4 * n);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "host to device copy");
+  s = run(ctx, false, (const uint8_t*)(d + o_q), q_bytes, (const int64_t*)(d + o_qo),
+          (const int32_t*)(d + o_ql), (const uint8_t*)(d + o_t), t_bytes,
+          (const int64_t*)(d + o_to), (const int32_t*)(d + o_tl), (const int32_t*)(d + o_h0),
+          n_pairs, sc, (xt_result*)(d + o_out), cells_out ? (int64_t*)(d + o_cells) : nullptr, st);
+  if (s != XT_OK) return s;
+  e = cudaMemcpyAsync(out, d + o_out, sizeof(xt_result) * n, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && cells_out)
+    e = cudaMemcpyAsync(cells_out, d + o_cells, 8 * n, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "device to host copy");
+  return XT_OK;
+}
+
+xt_status xt_ctx_set_schedule(xt_ctx* ctx, int P, int R) {
+  if (!ctx) return XT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (P == 0) {
+    ctx->forced_P = ctx->forced_R = 0;
+    return XT_OK;
+  }
+  const bool p_ok = P == 1 || P == 2 || P == 4 || P == 8 || P == 16 || P == 32;
+  const bool r_ok = R == 4 || R == 8 || (R == 16 && P <= 4);
+  if (!p_ok || !r_ok) return fail(ctx, XT_EINVAL, "unsupported schedule");
+  ctx->forced_P = P;
+  ctx->forced_R = R;
+  return XT_OK;
+}
+
+const char* xt_status_str(xt_status s) {
+  switch (s) {
+    case XT_OK: return "XT_OK";
+    case XT_EINVAL: return "XT_EINVAL";
+    case XT_ENOMEM: return "XT_ENOMEM";
+    case XT_ECUDA: return "XT_ECUDA";
+    case XT_ETIMEOUT: return "XT_ETIMEOUT";
+    case XT_EBUSY: return "XT_EBUSY";
+  }
+  return "XT_UNKNOWN";
+}
+
+const char* xt_ctx_last_error(const xt_ctx* ctx) {
+  return ctx ? ctx->last_error.c_str() : "";
+}
+
+}  // extern "C"

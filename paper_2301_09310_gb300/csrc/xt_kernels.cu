@@ -1,0 +1,237 @@
+// xt_kernels.cu -- classify/bucket, ordering, persistent queue kernels and the
+// plain one-pair-per-block kernel.
+#include <cstdio>
+
+#include "xt_engine.cuh"
+#include "xt_kernels.cuh"
+
+namespace xt {
+
+__device__ __forceinline__ int ceil_log2(uint32_t x) {  // x >= 1
+  return x <= 1 ? 0 : 32 - __clz(x - 1);
+}
+
+// ---------------------------------------------------------------- classify
+// Validates every pair, writes the results of invalid and degenerate pairs
+// directly, and assigns the others a class and a (bucket, sub-bucket) by
+// query length, counted for the ordering pass.
+__global__ void k_classify(Batch b, Score sc, int32_t match, Work w) {
+  const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= b.n) return;
+  const int64_t qo = b.q_off[k], to = b.t_off[k];
+  const int32_t ql = b.q_len[k], tl = b.t_len[k], h0 = b.h0[k];
+  const bool ok = h0 >= 1 && h0 <= XT_MAX_H0 && ql >= 0 && tl >= 0 && ql <= XT_MAX_LEN &&
+                  tl <= XT_MAX_LEN && qo >= 0 && to >= 0 && qo <= b.q_bytes - ql &&
+                  to <= b.t_bytes - tl;
+  if (!ok) {
+    write_result(b, k, 0, 0, 0, 0, 0, 0, XT_EINVAL, 0);
+    w.pclass[k] = CLS_DONE;
+    return;
+  }
+  if (ql == 0) {
+    write_result(b, k, h0, 0, 0, h0, 0, 0, XT_OK, 0);
+    w.pclass[k] = CLS_DONE;
+    return;
+  }
+  if (tl == 0) {
+    write_result(b, k, h0, 0, 0, -1, 0, 0, XT_OK, 0);
+    w.pclass[k] = CLS_DONE;
+    return;
+  }
+  int j = ceil_log2((uint32_t)ql + 2u);
+  if (j < kJMin) j = kJMin;
+  const int64_t bound = (int64_t)h0 + (int64_t)match * (ql < tl ? ql : tl);
+  const bool wide = bound > 32767 || ql > 65535;
+  int cls = wide ? CLS_WIDE : CLS_NARROW;
+  if (w.huge_j[j]) cls = CLS_HUGE;
+  const int32_t half = 1 << (j - 1);
+  int sub = (int)(((int64_t)(ql + 2 - half) * kNumSub) >> (j - 1));
+  sub = sub < 0 ? 0 : (sub >= kNumSub ? kNumSub - 1 : sub);
+  w.pclass[k] = (uint8_t)cls;
+  atomicAdd(&w.counts[(cls * kNumJ + j) * kNumSub + sub], 1);
+}
+
+// Exclusive scan of the bucket counts in queue order: per class, buckets from
+// the longest down, sub-buckets from the longest down (longest work first).
+__global__ void k_scan(Work w) {
+  if (threadIdx.x != 0) return;
+  int32_t acc = 0;
+  for (int cls = 0; cls < kNumClasses; ++cls) {
+    for (int j = kJMax; j >= 0; --j) {
+      w.seg_begin[cls * kNumJ + j] = acc;
+      for (int s = kNumSub - 1; s >= 0; --s) {
+        const int idx = (cls * kNumJ + j) * kNumSub + s;
+        w.cursor[idx] = acc;
+        acc += w.counts[idx];
+      }
+      w.seg_end[cls * kNumJ + j] = acc;
+    }
+  }
+}
+
+__global__ void k_scatter(Batch b, Work w) {
+  const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= b.n) return;
+  const int cls = w.pclass[k];
+  if (cls >= kNumClasses) return;
+  const int32_t ql = b.q_len[k];
+  int j = ceil_log2((uint32_t)ql + 2u);
+  if (j < kJMin) j = kJMin;
+  const int32_t half = 1 << (j - 1);
+  int sub = (int)(((int64_t)(ql + 2 - half) * kNumSub) >> (j - 1));
+  sub = sub < 0 ? 0 : (sub >= kNumSub ? kNumSub - 1 : sub);
+  const int32_t pos = atomicAdd(&w.cursor[(cls * kNumJ + j) * kNumSub + sub], 1);
+  w.order[pos] = k;
+}
+
+__device__ __forceinline__ Pair load_pair(const Batch& b, int32_t k) {
+  Pair pr;
+  pr.q = b.q_seq + b.q_off[k];
+  pr.t = b.t_seq + b.t_off[k];
+  pr.qlen = b.q_len[k];
+  pr.tlen = b.t_len[k];
+  pr.h0 = b.h0[k];
+  return pr;
+}
+
+// ------------------------------------------------------- persistent queue
+// Groups of P lanes pull pairs of class `cls`, buckets [j_lo, j_hi], from a
+// device-side queue (one atomicAdd per pair) until it is empty.
+template <int P, int R, bool WIDE>
+__global__ void __launch_bounds__(kQueueThreads)
+    k_queue(Batch b, Score sc, Work w, int cls, int j_lo, int j_hi, int head_id, int rs_log2,
+            int2* gring, int64_t slab) {
+  extern __shared__ int2 s_ring[];
+  __shared__ uint32_t s_prof[8];
+  if (threadIdx.x < 5) s_prof[threadIdx.x] = sc.prof[threadIdx.x];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int p = threadIdx.x % P;
+  const int g = threadIdx.x / P;
+  constexpr int G = kQueueThreads / P;
+  const unsigned gmask = (P == 32) ? 0xffffffffu : (((1u << P) - 1u) << (lane - p));
+  const int32_t begin = w.seg_begin[cls * kNumJ + j_hi];
+  const int32_t end = w.seg_end[cls * kNumJ + j_lo];
+  int2* ring;
+  int stride, rmask;
+  if (gring) {
+    ring = gring + (int64_t)(blockIdx.x * G + g) * slab;
+    stride = 1;
+    rmask = (int)(slab - 1);
+  } else {
+    ring = s_ring + g;
+    stride = G;
+    rmask = (1 << rs_log2) - 1;
+  }
+  int32_t* head = w.heads + head_id;
+  for (;;) {
+    int32_t idx = 0;
+    if (p == 0) idx = begin + atomicAdd(head, 1);
+    if (P > 1) idx = __shfl_sync(gmask, idx, 0, P);
+    if (idx >= end) break;
+    const int32_t k = w.order[idx];
+    const Pair pr = load_pair(b, k);
+    const Outcome o = run_pair<P, R, WIDE>(pr, sc, s_prof, ring, stride, rmask, p, gmask);
+    if (p == 0) write_result(b, k, o.score, o.qle, o.tle, o.gscore, o.gtle, o.max_off, XT_OK,
+                             o.cells);
+  }
+}
+
+// ------------------------------------------------------------------ plain
+// One pair per thread block of one warp (P = 32 lanes, R = 8 rows per lane),
+// 32-bit arithmetic, no bucketing: the comparison kernel.
+__global__ void __launch_bounds__(32) k_plain(Batch b, Score sc, Work w, int rs_log2) {
+  extern __shared__ int2 s_ring[];
+  __shared__ uint32_t s_prof[8];
+  const int32_t k = blockIdx.x;
+  const int cls = w.pclass[k];
+  if (cls != CLS_NARROW && cls != CLS_WIDE) return;
+  if (threadIdx.x < 5) s_prof[threadIdx.x] = sc.prof[threadIdx.x];
+  __syncwarp();
+  const Pair pr = load_pair(b, k);
+  const int rmask = (1 << rs_log2) - 1;
+  Outcome o;
+  if (cls == CLS_NARROW)
+    o = run_pair<32, 8, false>(pr, sc, s_prof, s_ring, 1, rmask, threadIdx.x, 0xffffffffu);
+  else
+    o = run_pair<32, 8, true>(pr, sc, s_prof, s_ring, 1, rmask, threadIdx.x, 0xffffffffu);
+  if (threadIdx.x == 0)
+    write_result(b, k, o.score, o.qle, o.tle, o.gscore, o.gtle, o.max_off, XT_OK, o.cells);
+}
+
+// ---------------------------------------------------------------- launchers
+cudaError_t launch_classify(const Batch& b, const Score& sc, int32_t match, const Work& w,
+                            cudaStream_t stream) {
+  if (b.n == 0) return cudaSuccess;
+  const int T = 256;
+  k_classify<<<(b.n + T - 1) / T, T, 0, stream>>>(b, sc, match, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_order(const Batch& b, const Work& w, cudaStream_t stream) {
+  k_scan<<<1, 32, 0, stream>>>(w);
+  if (b.n > 0) {
+    const int T = 256;
+    k_scatter<<<(b.n + T - 1) / T, T, 0, stream>>>(b, w);
+  }
+  return cudaGetLastError();
+}
+
+size_t queue_smem_bytes(int P, int rs_log2) {
+  return (size_t)(kQueueThreads / P) * ((size_t)1 << rs_log2) * sizeof(int2);
+}
+
+template <int P, int R, bool WIDE>
+static cudaError_t launch_queue_t(const Batch& b, const Score& sc, const Work& w, const Launch& L,
+                                  int head_id, int2* gring, cudaStream_t stream) {
+  const size_t smem = L.global_ring ? 0 : queue_smem_bytes(P, L.rs_log2);
+  auto kern = k_queue<P, R, WIDE>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<L.grid, kQueueThreads, smem, stream>>>(b, sc, w, L.cls, L.j_lo, L.j_hi, head_id,
+                                                L.rs_log2, L.global_ring ? gring : nullptr,
+                                                L.slab);
+  return cudaGetLastError();
+}
+
+template <bool WIDE>
+static cudaError_t launch_queue_w(const Batch& b, const Score& sc, const Work& w, const Launch& L,
+                                  int head_id, int2* gring, cudaStream_t stream) {
+#define XT_Q(PP, RR) \
+  if (L.P == PP && L.R == RR) return launch_queue_t<PP, RR, WIDE>(b, sc, w, L, head_id, gring, stream);
+  XT_Q(1, 8) XT_Q(2, 8) XT_Q(4, 8) XT_Q(8, 8) XT_Q(16, 8) XT_Q(32, 8)
+  XT_Q(1, 4) XT_Q(2, 4) XT_Q(4, 4) XT_Q(8, 4) XT_Q(16, 4) XT_Q(32, 4)
+  XT_Q(1, 16) XT_Q(2, 16) XT_Q(4, 16)
+#undef XT_Q
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_queue(const Batch& b, const Score& sc, const Work& w, const Launch& L,
+                         int head_id, int2* gring, cudaStream_t stream) {
+  if (L.cls == CLS_NARROW) return launch_queue_w<false>(b, sc, w, L, head_id, gring, stream);
+  return launch_queue_w<true>(b, sc, w, L, head_id, gring, stream);
+}
+
+cudaError_t launch_plain(const Batch& b, const Score& sc, const Work& w, int rs_log2,
+                         cudaStream_t stream) {
+  if (b.n == 0) return cudaSuccess;
+  const size_t smem = ((size_t)1 << rs_log2) * sizeof(int2);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_plain, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_plain<<<b.n, 32, smem, stream>>>(b, sc, w, rs_log2);
+  return cudaGetLastError();
+}
+
+int max_smem_per_block_optin(int device) {
+  int v = 0;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  return v;
+}
+
+}  // namespace xt

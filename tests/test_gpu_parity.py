@@ -1,0 +1,157 @@
+"""GPU parity: every field of every pair, bit-exact against the CPU oracle
+(integer DP: the tolerance is zero), called through the C ABI."""
+import numpy as np
+import pytest
+
+from paper_2301_09310_gb300 import synth
+from paper_2301_09310_gb300.synth import ScoringParams
+
+from tests.gpu_util import assert_same, batch_from_lists, fuzz_batch, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+SCHEDULES = [(1, 4), (1, 8), (1, 16), (2, 8), (4, 4), (4, 8), (4, 16), (8, 8), (16, 4), (32, 8)]
+
+SCORINGS = [
+    ScoringParams(),                                           # the workloads' scoring
+    ScoringParams(w=3, zdrop=5),
+    ScoringParams(w=0, zdrop=0),
+    ScoringParams(match=2, mismatch=-3, gap_open=2, gap_extend=2, w=12, zdrop=20, n_score=-2),
+    ScoringParams(match=3, mismatch=0, gap_open=0, gap_extend=0, w=7, zdrop=0, n_score=0),
+    ScoringParams(w=1000, zdrop=-1),
+]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    import paper_2301_09310_gb300 as xt
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = xt.Context(0)
+    yield c
+    c.close()
+
+
+def test_c1_tiny_batched_and_plain(ctx):
+    wl = synth.WORKLOADS["c1_tiny"]
+    b = synth.generate(wl)
+    want = run_oracle(b, wl.scoring)
+    assert_same(run_gpu(ctx, b, wl.scoring), want, "batched")
+    assert_same(run_gpu(ctx, b, wl.scoring, plain=True), want, "plain")
+
+
+@pytest.mark.parametrize("si", range(len(SCORINGS)))
+def test_fuzz_edges(ctx, si):
+    sc = SCORINGS[si]
+    b = fuzz_batch(100 + si, 1500)
+    want = run_oracle(b, sc)
+    assert_same(run_gpu(ctx, b, sc), want, f"batched {sc}")
+    assert_same(run_gpu(ctx, b, sc, plain=True), want, f"plain {sc}")
+
+
+@pytest.mark.parametrize("P,R", SCHEDULES)
+def test_schedule_invariance(ctx, P, R):
+    wl = synth.WORKLOADS["c3_mixed"]
+    b = synth.generate(wl, n=3000)
+    fz = fuzz_batch(7, 800, max_len=70, tail=60)
+    try:
+        ctx.set_schedule(P, R)
+        for batch, sc in ((b, wl.scoring), (fz, SCORINGS[1]), (fz, SCORINGS[3])):
+            assert_same(run_gpu(ctx, batch, sc), run_oracle(batch, sc), f"P={P} R={R} {sc}")
+    finally:
+        ctx.set_schedule(0)
+
+
+@pytest.mark.parametrize("name,n", [("c2_short", 40000), ("c3_mixed", 40000), ("c5_stream", 8000)])
+def test_workload_samples(ctx, name, n):
+    wl = synth.WORKLOADS[name]
+    b = synth.generate(wl, n=n)
+    want = run_oracle(b, wl.scoring)
+    assert_same(run_gpu(ctx, b, wl.scoring), want, f"{name} batched")
+    assert_same(run_gpu(ctx, b, wl.scoring, plain=True), want, f"{name} plain")
+
+
+def test_long_extensions(ctx):
+    wl = synth.WORKLOADS["c4_long"]
+    b = synth.generate(wl, n=48)
+    want = run_oracle(b, wl.scoring)
+    assert_same(run_gpu(ctx, b, wl.scoring), want, "c4 batched")
+    assert_same(run_gpu(ctx, b, wl.scoring, plain=True), want, "c4 plain")
+
+
+def test_huge_band_global_ring(ctx):
+    # a band wider than any shared-memory ring: queries longer than 4094
+    # with w = 6000 go to the global-slab kernel
+    rng = np.random.default_rng(5)
+    qs, ts, hs = [], [], []
+    for k in range(4):
+        q = rng.integers(0, 4, 4200 + 300 * k)
+        t = q.copy()
+        mut = rng.random(t.size) < 0.03
+        t[mut] = rng.integers(0, 4, int(mut.sum()))
+        qs.append(q)
+        ts.append(np.concatenate([t, rng.integers(0, 4, 500)]))
+        hs.append(30)
+    b = batch_from_lists(qs, ts, hs)
+    sc = ScoringParams(w=6000, zdrop=300)
+    want = run_oracle(b, sc)
+    assert_same(run_gpu(ctx, b, sc), want, "huge batched")
+    assert_same(run_gpu(ctx, b, sc, plain=True), want, "huge plain")
+
+
+def test_wide_scores(ctx):
+    # h0 near the limit pushes the score bound past 16 bits: the WIDE path
+    b = fuzz_batch(11, 600, max_len=60)
+    b.h0[:] = np.where(np.arange(b.n) % 2 == 0, 40000 + np.arange(b.n), b.h0)
+    b.h0[:] = np.minimum(b.h0, 1 << 20)
+    sc = SCORINGS[0]
+    want = run_oracle(b, sc)
+    assert_same(run_gpu(ctx, b, sc), want, "wide batched")
+    assert_same(run_gpu(ctx, b, sc, plain=True), want, "wide plain")
+
+
+def test_invalid_pairs(ctx):
+    b = fuzz_batch(12, 200)
+    b.h0[3] = 0
+    b.h0[4] = -5
+    b.h0[5] = (1 << 20) + 1
+    b.q_off[6] = b.q_seq.size + 10
+    b.t_len[7] = -1
+    b.q_len[8] = (1 << 20) + 1
+    b.t_off[9] = -1
+    sc = SCORINGS[0]
+    want = run_oracle(b, sc)
+    assert np.all(want[0][3:10, 6] == 1)
+    assert_same(run_gpu(ctx, b, sc), want, "invalid batched")
+    assert_same(run_gpu(ctx, b, sc, plain=True), want, "invalid plain")
+
+
+def test_bad_scoring_rejected(ctx):
+    import paper_2301_09310_gb300 as xt
+    b = fuzz_batch(13, 10)
+    with pytest.raises(xt.XtError) as e:
+        run_gpu(ctx, b, ScoringParams(match=0))
+    assert e.value.status == xt.XT_EINVAL
+
+
+def test_empty_batch(ctx):
+    b = batch_from_lists([], [], [])
+    out, cells = run_gpu(ctx, b, SCORINGS[0])
+    assert out.shape == (0, 7) and cells.shape == (0,)
+
+
+def test_host_variant(ctx):
+    wl = synth.WORKLOADS["c3_mixed"]
+    b = synth.generate(wl, n=5000)
+    out, cells = ctx.extend_host(b.q_seq, b.q_off, b.q_len, b.t_seq, b.t_off, b.t_len, b.h0,
+                                 wl.scoring)
+    assert_same((out, cells), run_oracle(b, wl.scoring), "host variant")
+
+
+def test_repeat_calls_reuse_workspace(ctx):
+    wl = synth.WORKLOADS["c2_short"]
+    b1 = synth.generate(wl, n=2000, first=0)
+    b2 = synth.generate(wl, n=7000, first=50000)
+    for b in (b2, b1, b2):
+        assert_same(run_gpu(ctx, b, wl.scoring), run_oracle(b, wl.scoring), "repeat")
