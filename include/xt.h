@@ -162,6 +162,24 @@ xt_status xt_extend_batch_host(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_byte
  */
 xt_status xt_ctx_set_schedule(xt_ctx* ctx, int P, int R);
 
+/*
+ * Launch accounting and DP timing (measurement aid).  With timing enabled,
+ * every extension call records a CUDA event pair on its stream around its DP
+ * (extension) kernels.  xt_ctx_stats waits for the pending events, sums their
+ * durations into dp_ms, reports the number of calls and kernel launches since
+ * the previous xt_ctx_stats, and resets those counters.
+ */
+typedef struct {
+  int32_t calls;        /* extension calls since the last query */
+  int32_t launches;     /* kernels those calls enqueued (classify, ordering, DP) */
+  int32_t dp_launches;  /* of which extension (DP) kernels */
+  int32_t timed_calls;  /* calls whose DP time is included in dp_ms */
+  double dp_ms;         /* summed device time of the DP kernels, ms */
+} xt_stats;
+
+xt_status xt_ctx_set_timing(xt_ctx* ctx, int enable);
+xt_status xt_ctx_stats(xt_ctx* ctx, xt_stats* out);
+
 /* Human-readable name of a status code (static storage). */
 const char* xt_status_str(xt_status s);
 

@@ -22,12 +22,18 @@ RESULT_FIELDS = ("score", "qle", "tle", "gscore", "gtle", "max_off", "status")
 
 EXPORTED = ("xt_ctx_create", "xt_ctx_destroy", "xt_ctx_sync", "xt_extend_batch",
             "xt_extend_batch_plain", "xt_extend_batch_host", "xt_status_str",
-            "xt_ctx_last_error", "xt_ctx_set_schedule")
+            "xt_ctx_last_error", "xt_ctx_set_schedule", "xt_ctx_set_timing", "xt_ctx_stats")
 
 
 class xt_scoring(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in
                 ("match", "mismatch", "gap_open", "gap_extend", "w", "zdrop", "n_score")]
+
+
+class xt_stats(ctypes.Structure):
+    _fields_ = [("calls", ctypes.c_int32), ("launches", ctypes.c_int32),
+                ("dp_launches", ctypes.c_int32), ("timed_calls", ctypes.c_int32),
+                ("dp_ms", ctypes.c_double)]
 
 
 class XtError(RuntimeError):
@@ -72,6 +78,10 @@ def load_library(path: str | None = None):
     lib.xt_status_str.restype = ctypes.c_char_p
     lib.xt_ctx_set_schedule.argtypes = [P, ctypes.c_int, ctypes.c_int]
     lib.xt_ctx_set_schedule.restype = ctypes.c_int
+    lib.xt_ctx_set_timing.argtypes = [P, ctypes.c_int]
+    lib.xt_ctx_set_timing.restype = ctypes.c_int
+    lib.xt_ctx_stats.argtypes = [P, ctypes.POINTER(xt_stats)]
+    lib.xt_ctx_stats.restype = ctypes.c_int
     lib.xt_ctx_last_error.argtypes = [P]
     lib.xt_ctx_last_error.restype = ctypes.c_char_p
     _LIB = lib
@@ -97,6 +107,18 @@ def xt_ctx_sync(ctx: int, stream: int = 0) -> int:
 
 def xt_ctx_set_schedule(ctx: int, P: int, R: int) -> int:
     return load_library().xt_ctx_set_schedule(ctypes.c_void_p(ctx), int(P), int(R))
+
+
+def xt_ctx_set_timing(ctx: int, enable: bool) -> int:
+    return load_library().xt_ctx_set_timing(ctypes.c_void_p(ctx), int(bool(enable)))
+
+
+def xt_ctx_stats(ctx: int) -> xt_stats:
+    st = xt_stats()
+    s = load_library().xt_ctx_stats(ctypes.c_void_p(ctx), ctypes.byref(st))
+    if s != XT_OK:
+        raise XtError(s, "xt_ctx_stats")
+    return st
 
 
 def xt_status_str(s: int) -> str:
@@ -184,6 +206,13 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def set_timing(self, enable: bool = True):
+        self._check(xt_ctx_set_timing(self.handle, enable), "xt_ctx_set_timing")
+
+    def stats(self) -> dict:
+        st = xt_ctx_stats(self.handle)
+        return {f: getattr(st, f) for f, _ in xt_stats._fields_}
 
     def set_schedule(self, P: int = 0, R: int = 8):
         self._check(xt_ctx_set_schedule(self.handle, P, R), "xt_ctx_set_schedule")

@@ -26,6 +26,12 @@ struct xt_ctx {
   // end-to-end staging: device copies of host inputs and pinned host mirrors
   void* dev_in = nullptr;
   size_t dev_in_bytes = 0;
+  // launch accounting and DP timing (xt_ctx_stats)
+  bool timing = false;
+  static constexpr int kEvRing = 256;
+  cudaEvent_t ev[kEvRing][2] = {};
+  int ev_pending = 0;
+  int calls = 0, launches = 0, dp_launches = 0;
   int forced_P = 0;              // schedule override (0: per-bucket table)
   int forced_R = 0;
   std::mutex mu;
@@ -286,14 +292,31 @@ xt_status run(xt_ctx* ctx, bool plain, const uint8_t* q_seq, int64_t q_bytes, co
   if (e != cudaSuccess) return cuda_fail(ctx, e, "classify");
   e = launch_order(b, w, stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "order");
+  const int slot = ctx->ev_pending;
+  const bool timed = ctx->timing && slot < xt_ctx::kEvRing;
+  if (timed) {
+    for (int k = 0; k < 2; ++k)
+      if (!ctx->ev[slot][k]) cudaEventCreate(&ctx->ev[slot][k]);
+    cudaEventRecord(ctx->ev[slot][0], stream);
+  }
+  int dp = 0;
   if (plain) {
     e = launch_plain(b, sc, w, plain_rs, stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "plain kernel");
+    ++dp;
   }
   for (int i = 0; i < pl.n_launch; ++i) {
     e = launch_queue(b, sc, w, pl.launch[i], i, ctx->pool, stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "queue kernel");
+    ++dp;
   }
+  if (timed) {
+    cudaEventRecord(ctx->ev[slot][1], stream);
+    ctx->ev_pending = slot + 1;
+  }
+  ctx->calls += 1;
+  ctx->launches += 3 + dp;  // classify, scan, scatter + DP kernels
+  ctx->dp_launches += dp;
   return XT_OK;
 }
 
@@ -326,6 +349,9 @@ xt_status xt_ctx_destroy(xt_ctx* ctx) {
   if (ctx->work) cudaFree(ctx->work);
   if (ctx->pool) cudaFree(ctx->pool);
   if (ctx->dev_in) cudaFree(ctx->dev_in);
+  for (auto& pr : ctx->ev)
+    for (auto& e : pr)
+      if (e) cudaEventDestroy(e);
   delete ctx;
   return XT_OK;
 }
@@ -408,6 +434,34 @@ xt_status xt_extend_batch_host(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_byte
     e = cudaMemcpyAsync(cells_out, d + o_cells, 8 * n, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "device to host copy");
+  return XT_OK;
+}
+
+xt_status xt_ctx_set_timing(xt_ctx* ctx, int enable) {
+  if (!ctx) return XT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->timing = enable != 0;
+  return XT_OK;
+}
+
+xt_status xt_ctx_stats(xt_ctx* ctx, xt_stats* out) {
+  if (!ctx || !out) return XT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  double ms = 0;
+  for (int i = 0; i < ctx->ev_pending; ++i) {
+    cudaError_t e = cudaEventSynchronize(ctx->ev[i][1]);
+    float t = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, ctx->ev[i][0], ctx->ev[i][1]);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "event timing");
+    ms += t;
+  }
+  out->calls = ctx->calls;
+  out->launches = ctx->launches;
+  out->dp_launches = ctx->dp_launches;
+  out->timed_calls = ctx->ev_pending;
+  out->dp_ms = ms;
+  ctx->calls = ctx->launches = ctx->dp_launches = 0;
+  ctx->ev_pending = 0;
   return XT_OK;
 }
 
