@@ -186,6 +186,40 @@ const char* xt_status_str(xt_status s);
 /* Last error message recorded by the context (static per context; "" if none). */
 const char* xt_ctx_last_error(const xt_ctx* ctx);
 
+/*
+ * Batched extension that allocates nothing (the paper has no counterpart:
+ * this exists for callers, not for the method).
+ *
+ * Some callers may not call cudaMalloc at all: code running inside another
+ * framework's memory pool or arena, a process that has reserved all of the
+ * device memory for itself up front, or a latency-critical loop that must
+ * never hit the allocator.  This entry point serves them: it takes no
+ * context and never allocates device or host memory.  Its scratch (the
+ * per-pair class bytes, the bucket queue and its counters) lives in one
+ * fixed array inside the library, XT_STATIC_SCRATCH_BYTES long, which every
+ * GPU that loads the library holds until the process exits.
+ *
+ * Arguments and results are those of xt_extend_batch (all arrays device
+ * memory of the CURRENT device, owned by the caller; work is enqueued on
+ * `stream`).  Limits, rejected with XT_EINVAL before anything is enqueued:
+ *   n_pairs <= XT_STATIC_MAX_PAIRS, and a band narrow enough that every
+ *   pair's boundary ring fits in shared memory (w up to about 1900; wider
+ *   bands need xt_extend_batch, which can grow a global ring pool).
+ * The first call on each device looks up the array's device address once
+ * (cudaGetSymbolAddress), so make that first call before any stream capture
+ * on that device.  All calls share the one array and it keeps the previous
+ * call's contents (the call zeroes what must start at zero): calls whose
+ * work overlaps on the GPU (other streams, other host threads) race on it,
+ * so order them, e.g. on one stream.
+ */
+#define XT_STATIC_MAX_PAIRS (1 << 20)
+#define XT_STATIC_SCRATCH_BYTES ((size_t)6 << 20)
+xt_status xt_extend_batch_static(const uint8_t* q_seq, int64_t q_bytes, const int64_t* q_off,
+                                 const int32_t* q_len, const uint8_t* t_seq, int64_t t_bytes,
+                                 const int64_t* t_off, const int32_t* t_len, const int32_t* h0,
+                                 int32_t n_pairs, const xt_scoring* sc, xt_result* out,
+                                 int64_t* cells_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,7 +22,9 @@ RESULT_FIELDS = ("score", "qle", "tle", "gscore", "gtle", "max_off", "status")
 
 EXPORTED = ("xt_ctx_create", "xt_ctx_destroy", "xt_ctx_sync", "xt_extend_batch",
             "xt_extend_batch_plain", "xt_extend_batch_host", "xt_status_str",
-            "xt_ctx_last_error", "xt_ctx_set_schedule", "xt_ctx_set_timing", "xt_ctx_stats")
+            "xt_ctx_last_error", "xt_ctx_set_schedule", "xt_ctx_set_timing", "xt_ctx_stats",
+            "xt_extend_batch_static")
+XT_STATIC_MAX_PAIRS = 1 << 20
 
 
 class xt_scoring(ctypes.Structure):
@@ -78,6 +80,8 @@ def load_library(path: str | None = None):
     lib.xt_status_str.restype = ctypes.c_char_p
     lib.xt_ctx_set_schedule.argtypes = [P, ctypes.c_int, ctypes.c_int]
     lib.xt_ctx_set_schedule.restype = ctypes.c_int
+    lib.xt_extend_batch_static.argtypes = batch_args[1:]
+    lib.xt_extend_batch_static.restype = ctypes.c_int
     lib.xt_ctx_set_timing.argtypes = [P, ctypes.c_int]
     lib.xt_ctx_set_timing.restype = ctypes.c_int
     lib.xt_ctx_stats.argtypes = [P, ctypes.POINTER(xt_stats)]
@@ -155,6 +159,19 @@ def xt_extend_batch_host(ctx, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_of
                          sc, out, cells, stream) -> int:
     return _call("xt_extend_batch_host", ctx, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off,
                  t_len, h0, n, sc, out, cells, stream)
+
+
+def xt_extend_batch_static(q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off, t_len, h0, n, sc,
+                           out, cells, stream) -> int:
+    """Allocation-free batched extension on the current device (no context):
+    for callers that may not allocate device memory.  Raw device pointers as
+    in include/xt.h; returns the xt_status.  Calls share one fixed scratch
+    array inside the library, so calls must not overlap on the GPU."""
+    return load_library().xt_extend_batch_static(
+        ctypes.c_void_p(q_seq), int(q_bytes), ctypes.c_void_p(q_off), ctypes.c_void_p(q_len),
+        ctypes.c_void_p(t_seq), int(t_bytes), ctypes.c_void_p(t_off), ctypes.c_void_p(t_len),
+        ctypes.c_void_p(h0), int(n), ctypes.byref(_scoring(sc)), ctypes.c_void_p(out),
+        ctypes.c_void_p(cells), ctypes.c_void_p(stream))
 
 
 # ------------------------------------------------------------ convenience

@@ -497,3 +497,109 @@ const char* xt_ctx_last_error(const xt_ctx* ctx) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------
+// Allocation-free batched extension (xt_extend_batch_static).
+//
+// The scratch the batched path needs -- one class byte and one int32 queue
+// slot per pair, bucket counters and cursors, the segment table, the queue
+// heads and the per-bucket flags -- is carved from this one fixed device
+// array instead of the context's workspace.  Host code only ever sees the
+// symbol as a host-side stand-in; the kernels get its device address, looked
+// up once per device below.
+static __device__ __align__(256) unsigned char g_static_scratch[XT_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_ptr[kStaticMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up on
+// the first call for that device).
+cudaError_t static_scratch(int device, void** ptr) {
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return e;
+    g_static_ptr[device] = p;
+  }
+  *ptr = g_static_ptr[device];
+  return cudaSuccess;
+}
+
+// Carve the Work tables for n pairs out of the scratch array; false if they
+// do not fit.
+bool carve_static(void* base_ptr, int32_t n, Work* w) {
+  size_t off = 0;
+  const size_t o_pclass = off; off = align_up(off + (size_t)n);
+  const size_t o_order = off; off = align_up(off + 4 * (size_t)n);
+  const size_t o_counts = off; off = align_up(off + 4 * (size_t)kNumBuckets);
+  const size_t o_cursor = off; off = align_up(off + 4 * (size_t)kNumBuckets);
+  const size_t o_sb = off; off = align_up(off + 4 * (size_t)(kNumClasses * kNumJ));
+  const size_t o_se = off; off = align_up(off + 4 * (size_t)(kNumClasses * kNumJ));
+  const size_t o_heads = off; off = align_up(off + 4 * (size_t)kMaxLaunches);
+  const size_t o_huge = off; off = align_up(off + (size_t)kNumJ);
+  if (off > XT_STATIC_SCRATCH_BYTES) return false;
+  char* base = (char*)base_ptr;
+  w->pclass = (uint8_t*)(base + o_pclass);
+  w->order = (int32_t*)(base + o_order);
+  w->counts = (int32_t*)(base + o_counts);
+  w->cursor = (int32_t*)(base + o_cursor);
+  w->seg_begin = (int32_t*)(base + o_sb);
+  w->seg_end = (int32_t*)(base + o_se);
+  w->heads = (int32_t*)(base + o_heads);
+  w->huge_j = (uint8_t*)(base + o_huge);
+  return true;
+}
+
+}  // namespace
+
+extern "C" xt_status xt_extend_batch_static(const uint8_t* q_seq, int64_t q_bytes,
+                                            const int64_t* q_off, const int32_t* q_len,
+                                            const uint8_t* t_seq, int64_t t_bytes,
+                                            const int64_t* t_off, const int32_t* t_len,
+                                            const int32_t* h0, int32_t n_pairs,
+                                            const xt_scoring* scr, xt_result* out,
+                                            int64_t* cells_out, void* stream) {
+  // A host-side context object only: it holds the launch plan's inputs and
+  // allocates nothing.
+  xt_ctx host;
+  xt_status s = check_args(&host, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off, t_len, h0,
+                           n_pairs, scr, out);
+  if (s != XT_OK) return s;
+  if (n_pairs > XT_STATIC_MAX_PAIRS) return XT_EINVAL;
+  if (n_pairs == 0) return XT_OK;
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kStaticMaxDevices)
+    return XT_ECUDA;
+  host.device = device;
+  if (cudaDeviceGetAttribute(&host.num_sms, cudaDevAttrMultiProcessorCount, device) !=
+      cudaSuccess)
+    return XT_ECUDA;
+  host.smem_optin = max_smem_per_block_optin(device);
+  const Score sc = make_score(scr);
+  Plan pl;
+  plan_batched(&host, sc, &pl);
+  if (pl.any_huge) return XT_EINVAL;  // band too wide for shared-memory rings
+  void* base = nullptr;
+  if (static_scratch(device, &base) != cudaSuccess) return XT_ECUDA;
+  Work w;
+  if (!carve_static(base, n_pairs, &w)) return XT_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  Batch b;
+  b.q_seq = q_seq; b.t_seq = t_seq; b.q_off = q_off; b.t_off = t_off; b.q_len = q_len;
+  b.t_len = t_len; b.h0 = h0; b.q_bytes = q_bytes; b.t_bytes = t_bytes; b.n = n_pairs; b.out = out;
+  b.cells = cells_out;
+  // counters and queue heads start at zero on every call; the bucket flags
+  // are rewritten; everything else is written before it is read
+  cudaError_t e = cudaMemsetAsync(w.counts, 0, 4 * (size_t)kNumBuckets, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.heads, 0, 4 * (size_t)kMaxLaunches, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.huge_j, 0, kNumJ, st);
+  if (e == cudaSuccess) e = launch_classify(b, sc, scr->match, w, st);
+  if (e == cudaSuccess) e = launch_order(b, w, st);
+  for (int i = 0; e == cudaSuccess && i < pl.n_launch; ++i)
+    e = launch_queue(b, sc, w, pl.launch[i], i, nullptr, st);
+  return e == cudaSuccess ? XT_OK : XT_ECUDA;
+}
