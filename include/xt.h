@@ -154,11 +154,13 @@ xt_status xt_extend_batch_host(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_byte
                                xt_result* out, int64_t* cells_out, void* stream);
 
 /*
- * Override the schedule of the batched path (testing and tuning aid).  P lanes
- * per pair (1, 2, 4, 8, 16 or 32) and R target rows per lane (4, 8, or 16 with
- * P <= 4) then apply to every length bucket whose ring still fits in shared
- * memory; P = 0 restores the built-in per-bucket table.  Results never depend
- * on the schedule.  XT_EINVAL for an unsupported (P, R).
+ * Override the schedule of the batched path (testing and tuning aid).
+ * P = 1 runs every bucket on the one-lane engine (one thread per pair, R rows
+ * per strip; packed pairs hold two stacked strips of R rows).  P = 2, 4, 8, 16
+ * or 32 runs the group engine (P lanes per pair, R rows per lane) on every
+ * bucket whose ring fits in shared memory.  R is 4, 8 or 16 (16 only with
+ * P <= 4).  P = 0 restores the built-in per-bucket table.  Results never
+ * depend on the schedule.  XT_EINVAL for an unsupported (P, R).
  */
 xt_status xt_ctx_set_schedule(xt_ctx* ctx, int P, int R);
 

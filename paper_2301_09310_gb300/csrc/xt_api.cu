@@ -32,6 +32,7 @@ struct xt_ctx {
   cudaEvent_t ev[kEvRing][2] = {};
   int ev_pending = 0;
   int calls = 0, launches = 0, dp_launches = 0;
+  int match = 1;                 // scoring of the call being planned
   int forced_P = 0;              // schedule override (0: per-bucket table)
   int forced_R = 0;
   std::mutex mu;
@@ -124,7 +125,6 @@ xt_status get_work(xt_ctx* ctx, int32_t n, Work* w) {
   const size_t o_sb = off; off = align_up(off + 4 * (size_t)(kNumClasses * kNumJ));
   const size_t o_se = off; off = align_up(off + 4 * (size_t)(kNumClasses * kNumJ));
   const size_t o_heads = off; off = align_up(off + 4 * (size_t)kMaxLaunches);
-  const size_t o_huge = off; off = align_up(off + (size_t)kNumJ);
   xt_status s = dev_alloc(ctx, &ctx->work, &ctx->work_bytes, off);
   if (s != XT_OK) return s;
   char* base = (char*)ctx->work;
@@ -135,14 +135,13 @@ xt_status get_work(xt_ctx* ctx, int32_t n, Work* w) {
   w->seg_begin = (int32_t*)(base + o_sb);
   w->seg_end = (int32_t*)(base + o_se);
   w->heads = (int32_t*)(base + o_heads);
-  w->huge_j = (uint8_t*)(base + o_huge);
   return XT_OK;
 }
 
 struct Plan {
   Launch launch[kMaxLaunches];
   int n_launch = 0;
-  uint8_t huge_j[kNumJ] = {0};
+  JFlags jf = {};
   bool any_huge = false;
   int64_t slab = 0;
 };
@@ -153,7 +152,7 @@ int64_t next_pow2(int64_t x) { return (int64_t)1 << log2_ceil(x); }
 // whose shared-memory ring fits 32 KB per CTA.  The ring needs
 // min(qlen, P*R + 2w) + 2 entries.
 void bucket_schedule(const xt_ctx* ctx, int j, int w, int* P, int* R, int* rs_log2, bool* huge) {
-  if (ctx->forced_P) {
+  if (ctx->forced_P > 1) {
     const int64_t need = std::min<int64_t>(
         (int64_t)1 << j, next_pow2((int64_t)ctx->forced_P * ctx->forced_R + 2 * (int64_t)w + 2));
     const int lg = log2_ceil(need);
@@ -189,38 +188,95 @@ void add_huge_launch(xt_ctx* ctx, const Score& sc, Plan* pl) {
   L.global_ring = true; L.slab = pl->slab; L.grid = (int)grid;
 }
 
-void plan_batched(xt_ctx* ctx, const Score& sc, Plan* pl) {
-  for (int cls = CLS_NARROW; cls <= CLS_WIDE; ++cls) {
+constexpr int kLaneJMax = 9;           // one-lane engine for queries up to 2^9 - 2 bases
+constexpr size_t kLaneSmemCap = 48 * 1024;
+
+// One-lane launch of bucket j for class cls (PACKED or NARROW); false if it
+// needs a global ring and those are not allowed.
+bool lane_launch(xt_ctx* ctx, const Score& sc, int cls, int j, bool allow_gring, Launch* L) {
+  const int R = ctx->forced_P == 1 ? ctx->forced_R : 8;
+  const int rows = cls == CLS_PACKED ? 2 * R : R;
+  const int64_t need = std::min<int64_t>((int64_t)1 << j, next_pow2(rows + 2 * (int64_t)sc.w + 2));
+  const int lg = log2_ceil(need);
+  const size_t smem = (size_t)kLaneThreads * lane_ring_bytes(cls, lg);
+  const bool gring = smem > kLaneSmemCap;
+  if (gring && !allow_gring) return false;
+  L->cls = cls; L->j_lo = j; L->j_hi = j; L->lane = true; L->P = 1; L->R = R;
+  L->rs_log2 = lg; L->global_ring = gring; L->slab = gring ? ((int64_t)1 << lg) : 0;
+  const int per_sm = gring ? 4 : (int)std::max<size_t>(1, std::min<size_t>(8, (size_t)(200 * 1024) / (smem + 1024)));
+  L->grid = ctx->num_sms * per_sm;
+  int k = 0;
+  while ((1 << k) < ctx->match + 1) ++k;
+  L->mparam = cls == CLS_PACKED ? k : ctx->match + 1;
+  return true;
+}
+
+bool same_config(const Launch& a, const Launch& b) {
+  return a.cls == b.cls && a.lane == b.lane && a.P == b.P && a.R == b.R &&
+         a.rs_log2 == b.rs_log2 && a.global_ring == b.global_ring && a.grid == b.grid &&
+         a.mparam == b.mparam;
+}
+
+void plan_batched(xt_ctx* ctx, const Score& sc, Plan* pl, bool allow_gring = true) {
+  // which buckets run the one-lane engine (the same answer for every class)
+  bool lane_j[kNumJ] = {false};
+  for (int j = kJMin; j <= kJMax; ++j) {
+    Launch L;
+    const bool want = ctx->forced_P == 1 || (!ctx->forced_P && j <= kLaneJMax);
+    lane_j[j] = want &&
+                lane_launch(ctx, sc, CLS_PACKED, j, allow_gring, &L) &&
+                lane_launch(ctx, sc, CLS_NARROW, j, allow_gring, &L);
+    if (lane_j[j]) pl->jf.f[j] |= kJPacked;
+  }
+  for (int cls = CLS_PACKED; cls <= CLS_WIDE; ++cls) {
     int prev = -1;
     for (int j = kJMax; j >= kJMin; --j) {
-      int P, R, lg;
-      bool huge;
-      bucket_schedule(ctx, j, sc.w, &P, &R, &lg, &huge);
-      if (huge) {
-        pl->huge_j[j] = 1;
-        pl->any_huge = true;
-        prev = -1;
-        continue;
-      }
-      if (prev >= 0) {
-        Launch& L = pl->launch[prev];
-        if (L.P == P && L.R == R && L.rs_log2 == lg) {
-          L.j_lo = j;
+      Launch L;
+      if (lane_j[j] && cls != CLS_WIDE) {
+        lane_launch(ctx, sc, cls, j, allow_gring, &L);
+      } else {
+        if (cls == CLS_PACKED) { prev = -1; continue; }  // no packed pairs in this bucket
+        int P, R, lg;
+        bool huge;
+        bucket_schedule(ctx, j, sc.w, &P, &R, &lg, &huge);
+        if (huge) {
+          pl->jf.f[j] |= kJHuge;
+          pl->any_huge = true;
+          prev = -1;
           continue;
         }
+        L.cls = cls; L.j_lo = j; L.j_hi = j; L.lane = false; L.P = P; L.R = R;
+        L.rs_log2 = lg; L.global_ring = false; L.slab = 0; L.mparam = 0;
+        const size_t smem = queue_smem_bytes(P, lg);
+        const int per_sm = (int)std::min<size_t>(16, std::max<size_t>(1, (size_t)(220 * 1024) / std::max<size_t>(smem + 1024, 1)));
+        L.grid = ctx->num_sms * per_sm;
       }
-      Launch& L = pl->launch[pl->n_launch];
-      L.cls = cls; L.j_lo = j; L.j_hi = (j == kJMax ? kJMax : j); L.P = P; L.R = R;
-      L.rs_log2 = lg; L.global_ring = false; L.slab = 0;
-      const size_t smem = queue_smem_bytes(P, lg);
-      int per_sm = (int)std::min<size_t>(16, std::max<size_t>(1, (size_t)(220 * 1024) / std::max<size_t>(smem + 1024, 1)));
-      L.grid = ctx->num_sms * per_sm;
+      if (prev >= 0 && same_config(pl->launch[prev], L)) {
+        pl->launch[prev].j_lo = j;
+        continue;
+      }
+      pl->launch[pl->n_launch] = L;
       prev = pl->n_launch++;
     }
     // the lowest bucket also takes the pairs below kJMin (classify clamps j)
     if (prev >= 0) pl->launch[prev].j_lo = 0;
   }
   if (pl->any_huge) add_huge_launch(ctx, sc, pl);
+}
+
+// Device bytes the global-ring launches of a plan need (they run one after
+// another on the stream and share one pool).
+size_t pool_bytes(const Plan& pl) {
+  size_t need = 0;
+  for (int i = 0; i < pl.n_launch; ++i) {
+    const Launch& L = pl.launch[i];
+    if (!L.global_ring) continue;
+    size_t b;
+    if (L.lane) b = (size_t)L.grid * kLaneThreads * (size_t)L.slab * lane_ring_bytes(L.cls, 0);
+    else b = (size_t)L.grid * (kQueueThreads / L.P) * (size_t)L.slab * sizeof(int2);
+    need = std::max(need, b);
+  }
+  return need;
 }
 
 void plan_plain(xt_ctx* ctx, const Score& sc, Plan* pl, int* rs_log2) {
@@ -232,7 +288,7 @@ void plan_plain(xt_ctx* ctx, const Score& sc, Plan* pl, int* rs_log2) {
     // a pair of bucket j needs at most min(2^j, 256 + 2w + 2) ring entries
     const int64_t nj = std::min<int64_t>((int64_t)1 << j, next_pow2(need));
     if (nj > ((int64_t)1 << lg)) {
-      pl->huge_j[j] = 1;
+      pl->jf.f[j] |= kJHuge;
       pl->any_huge = true;
     }
   }
@@ -270,11 +326,11 @@ xt_status run(xt_ctx* ctx, bool plain, const uint8_t* q_seq, int64_t q_bytes, co
   if (s != XT_OK) return s;
   Plan pl;
   int plain_rs = 0;
+  ctx->match = scr->match;
   if (plain) plan_plain(ctx, sc, &pl, &plain_rs);
   else plan_batched(ctx, sc, &pl);
-  if (pl.any_huge) {
-    const size_t want = (size_t)pl.launch[pl.n_launch - 1].grid * (kQueueThreads / 32) *
-                        (size_t)pl.slab * sizeof(int2);
+  const size_t want = pool_bytes(pl);
+  if (want) {
     s = dev_alloc(ctx, (void**)&ctx->pool, &ctx->pool_bytes, want);
     if (s != XT_OK) return s;
   }
@@ -285,10 +341,8 @@ xt_status run(xt_ctx* ctx, bool plain, const uint8_t* q_seq, int64_t q_bytes, co
   // small control block: counts, heads and the bucket flags
   e = cudaMemsetAsync(w.counts, 0, 4 * (size_t)kNumBuckets, stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(w.heads, 0, 4 * (size_t)kMaxLaunches, stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(w.huge_j, pl.huge_j, kNumJ, cudaMemcpyHostToDevice, stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "workspace init");
-  e = launch_classify(b, sc, scr->match, w, stream);
+  e = launch_classify(b, sc, scr->match, pl.jf, w, stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "classify");
   e = launch_order(b, w, stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "order");
@@ -306,8 +360,10 @@ xt_status run(xt_ctx* ctx, bool plain, const uint8_t* q_seq, int64_t q_bytes, co
     ++dp;
   }
   for (int i = 0; i < pl.n_launch; ++i) {
-    e = launch_queue(b, sc, w, pl.launch[i], i, ctx->pool, stream);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "queue kernel");
+    const Launch& L = pl.launch[i];
+    e = L.lane ? launch_lane(b, sc, w, L, i, ctx->pool, stream)
+               : launch_queue(b, sc, w, L, i, ctx->pool, stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, L.lane ? "lane kernel" : "queue kernel");
     ++dp;
   }
   if (timed) {
@@ -540,7 +596,6 @@ bool carve_static(void* base_ptr, int32_t n, Work* w) {
   const size_t o_sb = off; off = align_up(off + 4 * (size_t)(kNumClasses * kNumJ));
   const size_t o_se = off; off = align_up(off + 4 * (size_t)(kNumClasses * kNumJ));
   const size_t o_heads = off; off = align_up(off + 4 * (size_t)kMaxLaunches);
-  const size_t o_huge = off; off = align_up(off + (size_t)kNumJ);
   if (off > XT_STATIC_SCRATCH_BYTES) return false;
   char* base = (char*)base_ptr;
   w->pclass = (uint8_t*)(base + o_pclass);
@@ -550,7 +605,6 @@ bool carve_static(void* base_ptr, int32_t n, Work* w) {
   w->seg_begin = (int32_t*)(base + o_sb);
   w->seg_end = (int32_t*)(base + o_se);
   w->heads = (int32_t*)(base + o_heads);
-  w->huge_j = (uint8_t*)(base + o_huge);
   return true;
 }
 
@@ -581,7 +635,8 @@ extern "C" xt_status xt_extend_batch_static(const uint8_t* q_seq, int64_t q_byte
   host.smem_optin = max_smem_per_block_optin(device);
   const Score sc = make_score(scr);
   Plan pl;
-  plan_batched(&host, sc, &pl);
+  host.match = scr->match;
+  plan_batched(&host, sc, &pl, /*allow_gring=*/false);
   if (pl.any_huge) return XT_EINVAL;  // band too wide for shared-memory rings
   void* base = nullptr;
   if (static_scratch(device, &base) != cudaSuccess) return XT_ECUDA;
@@ -596,10 +651,11 @@ extern "C" xt_status xt_extend_batch_static(const uint8_t* q_seq, int64_t q_byte
   // are rewritten; everything else is written before it is read
   cudaError_t e = cudaMemsetAsync(w.counts, 0, 4 * (size_t)kNumBuckets, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(w.heads, 0, 4 * (size_t)kMaxLaunches, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(w.huge_j, 0, kNumJ, st);
-  if (e == cudaSuccess) e = launch_classify(b, sc, scr->match, w, st);
+  if (e == cudaSuccess) e = launch_classify(b, sc, scr->match, pl.jf, w, st);
   if (e == cudaSuccess) e = launch_order(b, w, st);
-  for (int i = 0; e == cudaSuccess && i < pl.n_launch; ++i)
-    e = launch_queue(b, sc, w, pl.launch[i], i, nullptr, st);
+  for (int i = 0; e == cudaSuccess && i < pl.n_launch; ++i) {
+    const Launch& L = pl.launch[i];
+    e = L.lane ? launch_lane(b, sc, w, L, i, nullptr, st) : launch_queue(b, sc, w, L, i, nullptr, st);
+  }
   return e == cudaSuccess ? XT_OK : XT_ECUDA;
 }

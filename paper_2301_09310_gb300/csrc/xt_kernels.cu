@@ -4,6 +4,7 @@
 
 #include "xt_engine.cuh"
 #include "xt_kernels.cuh"
+#include "xt_lane.cuh"
 
 namespace xt {
 
@@ -15,7 +16,7 @@ __device__ __forceinline__ int ceil_log2(uint32_t x) {  // x >= 1
 // Validates every pair, writes the results of invalid and degenerate pairs
 // directly, and assigns the others a class and a (bucket, sub-bucket) by
 // query length, counted for the ordering pass.
-__global__ void k_classify(Batch b, Score sc, int32_t match, Work w) {
+__global__ void k_classify(Batch b, Score sc, int32_t match, int32_t mshift, JFlags jfl, Work w) {
   const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= b.n) return;
   const int64_t qo = b.q_off[k], to = b.t_off[k];
@@ -42,8 +43,10 @@ __global__ void k_classify(Batch b, Score sc, int32_t match, Work w) {
   if (j < kJMin) j = kJMin;
   const int64_t bound = (int64_t)h0 + (int64_t)match * (ql < tl ? ql : tl);
   const bool wide = bound > 32767 || ql > 65535;
+  const uint8_t jf = jfl.f[j];
   int cls = wide ? CLS_WIDE : CLS_NARROW;
-  if (w.huge_j[j]) cls = CLS_HUGE;
+  if (!wide && (jf & kJPacked) && ((bound + 1) << mshift) <= 32767) cls = CLS_PACKED;
+  if (jf & kJHuge) cls = CLS_HUGE;
   const int32_t half = 1 << (j - 1);
   int sub = (int)(((int64_t)(ql + 2 - half) * kNumSub) >> (j - 1));
   sub = sub < 0 ? 0 : (sub >= kNumSub ? kNumSub - 1 : sub);
@@ -137,6 +140,50 @@ __global__ void __launch_bounds__(kQueueThreads)
   }
 }
 
+// --------------------------------------------------------- one-lane queue
+// Every lane extends whole pairs on its own; the warp takes consecutive queue
+// slots (one atomicAdd per warp per round), so neighbouring lanes get pairs
+// of nearly equal length.
+template <int R, bool PACKED, bool GRING>
+__global__ void __launch_bounds__(kLaneThreads)
+    k_lane(Batch b, Score sc, Work w, int cls, int j_lo, int j_hi, int head_id, int rs_log2,
+           void* gring, int mparam) {
+  using T = typename Ring<PACKED>::T;
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  __shared__ uint32_t s_prof[8];
+  if (threadIdx.x < 5) s_prof[threadIdx.x] = sc.prof[threadIdx.x];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  Ring<PACKED> ring;
+  ring.mask = (1 << rs_log2) - 1;
+  if (GRING) {
+    ring.base = reinterpret_cast<T*>(gring) +
+                ((int64_t)blockIdx.x * kLaneThreads + threadIdx.x) * ((int64_t)1 << rs_log2);
+    ring.stride = 1;
+  } else {
+    ring.base = reinterpret_cast<T*>(s_dyn) + threadIdx.x;
+    ring.stride = kLaneThreads;
+  }
+  const int32_t begin = w.seg_begin[cls * kNumJ + j_hi];
+  const int32_t end = w.seg_end[cls * kNumJ + j_lo];
+  int32_t* head = w.heads + head_id;
+  for (;;) {
+    const unsigned act = __activemask();
+    const int leader = __ffs(act) - 1;
+    int32_t base = 0;
+    if (lane == leader) base = atomicAdd(head, __popc(act));
+    base = __shfl_sync(act, base, leader);
+    const int32_t idx = begin + base + __popc(act & ((1u << lane) - 1u));
+    if (idx >= end) break;
+    const int32_t k = w.order[idx];
+    const Pair pr = load_pair(b, k);
+    Outcome o;
+    if (PACKED) o = lane_pair_p16<R>(pr, sc, s_prof, *reinterpret_cast<Ring<true>*>(&ring), mparam);
+    else o = lane_pair_i32<R>(pr, sc, s_prof, *reinterpret_cast<Ring<false>*>(&ring), mparam);
+    write_result(b, k, o.score, o.qle, o.tle, o.gscore, o.gtle, o.max_off, XT_OK, o.cells);
+  }
+}
+
 // ------------------------------------------------------------------ plain
 // One pair per thread block of one warp (P = 32 lanes, R = 8 rows per lane),
 // 32-bit arithmetic, no bucketing: the comparison kernel.
@@ -160,11 +207,13 @@ __global__ void __launch_bounds__(32) k_plain(Batch b, Score sc, Work w, int rs_
 }
 
 // ---------------------------------------------------------------- launchers
-cudaError_t launch_classify(const Batch& b, const Score& sc, int32_t match, const Work& w,
-                            cudaStream_t stream) {
+cudaError_t launch_classify(const Batch& b, const Score& sc, int32_t match, const JFlags& jf,
+                            const Work& w, cudaStream_t stream) {
   if (b.n == 0) return cudaSuccess;
   const int T = 256;
-  k_classify<<<(b.n + T - 1) / T, T, 0, stream>>>(b, sc, match, w);
+  int mshift = 0;
+  while ((1 << mshift) < match + 1) ++mshift;
+  k_classify<<<(b.n + T - 1) / T, T, 0, stream>>>(b, sc, match, mshift, jf, w);
   return cudaGetLastError();
 }
 
@@ -213,6 +262,41 @@ cudaError_t launch_queue(const Batch& b, const Score& sc, const Work& w, const L
                          int head_id, int2* gring, cudaStream_t stream) {
   if (L.cls == CLS_NARROW) return launch_queue_w<false>(b, sc, w, L, head_id, gring, stream);
   return launch_queue_w<true>(b, sc, w, L, head_id, gring, stream);
+}
+
+size_t lane_ring_bytes(int cls, int rs_log2) {
+  return ((size_t)1 << rs_log2) * (cls == CLS_PACKED ? sizeof(uint32_t) : sizeof(int2));
+}
+
+template <int R, bool PACKED, bool GRING>
+static cudaError_t launch_lane_t(const Batch& b, const Score& sc, const Work& w, const Launch& L,
+                                 int head_id, void* gring, cudaStream_t stream) {
+  const size_t smem = GRING ? 0 : kLaneThreads * lane_ring_bytes(L.cls, L.rs_log2);
+  auto kern = k_lane<R, PACKED, GRING>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<L.grid, kLaneThreads, smem, stream>>>(b, sc, w, L.cls, L.j_lo, L.j_hi, head_id,
+                                               L.rs_log2, gring, L.mparam);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lane(const Batch& b, const Score& sc, const Work& w, const Launch& L,
+                        int head_id, void* gring, cudaStream_t stream) {
+  const bool packed = L.cls == CLS_PACKED;
+#define XT_L(RR)                                                                         \
+  if (L.R == RR) {                                                                       \
+    if (packed)                                                                          \
+      return L.global_ring ? launch_lane_t<RR, true, true>(b, sc, w, L, head_id, gring, stream) \
+                           : launch_lane_t<RR, true, false>(b, sc, w, L, head_id, gring, stream); \
+    return L.global_ring ? launch_lane_t<RR, false, true>(b, sc, w, L, head_id, gring, stream) \
+                         : launch_lane_t<RR, false, false>(b, sc, w, L, head_id, gring, stream); \
+  }
+  XT_L(4) XT_L(8) XT_L(16)
+#undef XT_L
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_plain(const Batch& b, const Score& sc, const Work& w, int rs_log2,

@@ -9,8 +9,15 @@
 namespace xt {
 
 // Pair classes after classify.
-enum PairClass : uint8_t { CLS_NARROW = 0, CLS_WIDE = 1, CLS_HUGE = 2, CLS_DONE = 3 };
-constexpr int kNumClasses = 3;           // classes that need a DP kernel
+//   PACKED: two strips in the 16-bit halves of each register (one-lane engine)
+//   NARROW: 32-bit, row key H*65536 + j (h0 + match*min(qlen,tlen) <= 32767)
+//   WIDE:   32-bit with an explicit (max, column) pair per row
+//   HUGE:   band ring too large for shared memory (global slab per group)
+enum PairClass : uint8_t { CLS_PACKED = 0, CLS_NARROW = 1, CLS_WIDE = 2, CLS_HUGE = 3, CLS_DONE = 4 };
+constexpr int kNumClasses = 4;           // classes that need a DP kernel
+// per-bucket flags (Work::jflags)
+constexpr uint8_t kJHuge = 1;            // bucket's pairs go to the HUGE class
+constexpr uint8_t kJPacked = 2;          // bucket runs the one-lane engine: packed pairs allowed
 constexpr int kJMin = 5;                 // length buckets j: qlen + 2 <= 2^j
 constexpr int kJMax = 21;
 constexpr int kNumJ = kJMax + 1;
@@ -28,29 +35,40 @@ struct Work {
   int32_t* seg_begin;   // [kNumClasses * kNumJ]
   int32_t* seg_end;     // [kNumClasses * kNumJ]
   int32_t* heads;       // [kMaxLaunches]
-  uint8_t* huge_j;      // [kNumJ] 1 if bucket j goes to the global-ring kernel
 };
 
-// One persistent queue-kernel launch: pairs of class cls, buckets [j_lo, j_hi].
+constexpr int kLaneThreads = 128;        // threads per CTA of the one-lane kernels
+
+// One persistent launch: pairs of class cls, buckets [j_lo, j_hi].
 struct Launch {
   int cls, j_lo, j_hi;
-  int P, R;            // lanes per pair, rows per lane-strip
-  int rs_log2;         // ring entries per group = 1 << rs_log2 (shared memory)
-  bool global_ring;    // huge pairs: ring in a global slab per group
+  bool lane;           // one-lane engine (k_lane) instead of the group engine (k_queue)
+  int P, R;            // lanes per pair, rows per lane-strip (per half when packed)
+  int rs_log2;         // ring entries per group = 1 << rs_log2
+  bool global_ring;    // ring in a global slab per group instead of shared memory
   int64_t slab;        // entries per global slab (power of two)
   int grid;            // CTAs
+  int mparam;          // one-lane engine: match + 1 (32-bit) or shift k (packed)
 };
 
 // Host-side launchers (defined in xt_kernels.cu); all enqueue on `stream`.
-cudaError_t launch_classify(const Batch& b, const Score& sc, int32_t match, const Work& w,
-                            cudaStream_t stream);
+// Per-bucket flags (kJHuge | kJPacked), passed to classify by value.
+struct JFlags {
+  uint8_t f[kNumJ];
+};
+cudaError_t launch_classify(const Batch& b, const Score& sc, int32_t match, const JFlags& jf,
+                            const Work& w, cudaStream_t stream);
 cudaError_t launch_order(const Batch& b, const Work& w, cudaStream_t stream);
 cudaError_t launch_queue(const Batch& b, const Score& sc, const Work& w, const Launch& L,
                          int head_id, int2* gring, cudaStream_t stream);
 cudaError_t launch_plain(const Batch& b, const Score& sc, const Work& w, int rs_log2,
                          cudaStream_t stream);
+cudaError_t launch_lane(const Batch& b, const Score& sc, const Work& w, const Launch& L,
+                        int head_id, void* gring, cudaStream_t stream);
 // Shared memory a queue launch needs per CTA (bytes).
 size_t queue_smem_bytes(int P, int rs_log2);
+// Ring bytes per lane of a one-lane launch (per CTA in shared memory: x kLaneThreads).
+size_t lane_ring_bytes(int cls, int rs_log2);
 int max_smem_per_block_optin(int device);
 
 }  // namespace xt
