@@ -12,6 +12,23 @@ __device__ __forceinline__ int ceil_log2(uint32_t x) {  // x >= 1
   return x <= 1 ? 0 : 32 - __clz(x - 1);
 }
 
+// Length bucket j (qlen + 2 <= 2^j, at least kJMin) and sub-bucket: the exact
+// query length while a bucket spans at most kNumSub lengths, else its top bits.
+__device__ __forceinline__ void bucket_of(int32_t ql, int* j_out, int* sub_out) {
+  int j = ceil_log2((uint32_t)ql + 2u);
+  if (j < kJMin) j = kJMin;
+  int sub;
+  if (j == kJMin) {
+    sub = ql;
+  } else {
+    const int32_t off = ql + 2 - (1 << (j - 1));
+    sub = j <= 9 ? off : (off >> (j - 9));
+  }
+  sub = sub < 0 ? 0 : (sub >= kNumSub ? kNumSub - 1 : sub);
+  *j_out = j;
+  *sub_out = sub;
+}
+
 // ---------------------------------------------------------------- classify
 // Validates every pair, writes the results of invalid and degenerate pairs
 // directly, and assigns the others a class and a (bucket, sub-bucket) by
@@ -39,35 +56,78 @@ __global__ void k_classify(Batch b, Score sc, int32_t match, int32_t mshift, JFl
     w.pclass[k] = CLS_DONE;
     return;
   }
-  int j = ceil_log2((uint32_t)ql + 2u);
-  if (j < kJMin) j = kJMin;
+  int j, sub;
+  bucket_of(ql, &j, &sub);
   const int64_t bound = (int64_t)h0 + (int64_t)match * (ql < tl ? ql : tl);
   const bool wide = bound > 32767 || ql > 65535;
   const uint8_t jf = jfl.f[j];
   int cls = wide ? CLS_WIDE : CLS_NARROW;
-  if (!wide && (jf & kJPacked) && ((bound + 1) << mshift) <= 32767) cls = CLS_PACKED;
+  // packed: the anchoring multiply and the 16-bit row keys (H * 32 + step) fit
+  if (!wide && (jf & kJPacked) && ((bound + 1) << mshift) <= 32767 && bound * 32 + 31 <= 32767)
+    cls = CLS_PACKED;
   if (jf & kJHuge) cls = CLS_HUGE;
-  const int32_t half = 1 << (j - 1);
-  int sub = (int)(((int64_t)(ql + 2 - half) * kNumSub) >> (j - 1));
-  sub = sub < 0 ? 0 : (sub >= kNumSub ? kNumSub - 1 : sub);
   w.pclass[k] = (uint8_t)cls;
   atomicAdd(&w.counts[(cls * kNumJ + j) * kNumSub + sub], 1);
 }
 
 // Exclusive scan of the bucket counts in queue order: per class, buckets from
 // the longest down, sub-buckets from the longest down (longest work first).
-__global__ void k_scan(Work w) {
-  if (threadIdx.x != 0) return;
-  int32_t acc = 0;
-  for (int cls = 0; cls < kNumClasses; ++cls) {
-    for (int j = kJMax; j >= 0; --j) {
-      w.seg_begin[cls * kNumJ + j] = acc;
-      for (int s = kNumSub - 1; s >= 0; --s) {
-        const int idx = (cls * kNumJ + j) * kNumSub + s;
-        w.cursor[idx] = acc;
-        acc += w.counts[idx];
-      }
-      w.seg_end[cls * kNumJ + j] = acc;
+// One block of kScanThreads threads, each owning a run of counters.
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = (kNumBuckets + kScanThreads - 1) / kScanThreads;
+
+__device__ __forceinline__ int scan_index(int L) {  // queue position -> counter index
+  const int per_cls = kNumJ * kNumSub;
+  const int cls = L / per_cls;
+  const int rem = L - cls * per_cls;
+  const int j = kJMax - rem / kNumSub;
+  const int sub = kNumSub - 1 - rem % kNumSub;
+  return (cls * kNumJ + j) * kNumSub + sub;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan(Work w) {
+  __shared__ int32_t s_warp[kScanThreads / 32];
+  const int t = threadIdx.x;
+  int32_t vals[kScanPer];
+  int32_t sum = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    const int L = t * kScanPer + k;
+    vals[k] = L < kNumBuckets ? w.counts[scan_index(L)] : 0;
+    sum += vals[k];
+  }
+  // block-wide exclusive scan of the per-thread sums
+  const int lane = t & 31, wid = t >> 5;
+  int32_t incl = sum;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int32_t v = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += v;
+  }
+  if (lane == 31) s_warp[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    int32_t v = s_warp[lane];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int32_t u = __shfl_up_sync(0xffffffffu, v, d);
+      if (lane >= d) v += u;
+    }
+    s_warp[lane] = v;  // inclusive warp totals
+  }
+  __syncthreads();
+  int32_t acc = incl - sum + (wid > 0 ? s_warp[wid - 1] : 0);
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    const int L = t * kScanPer + k;
+    if (L < kNumBuckets) {
+      const int idx = scan_index(L);
+      const int cj = idx / kNumSub;  // cls * kNumJ + j
+      const int sub = idx % kNumSub;
+      w.cursor[idx] = acc;
+      if (sub == kNumSub - 1) w.seg_begin[cj] = acc;
+      acc += vals[k];
+      if (sub == 0) w.seg_end[cj] = acc;
     }
   }
 }
@@ -78,11 +138,8 @@ __global__ void k_scatter(Batch b, Work w) {
   const int cls = w.pclass[k];
   if (cls >= kNumClasses) return;
   const int32_t ql = b.q_len[k];
-  int j = ceil_log2((uint32_t)ql + 2u);
-  if (j < kJMin) j = kJMin;
-  const int32_t half = 1 << (j - 1);
-  int sub = (int)(((int64_t)(ql + 2 - half) * kNumSub) >> (j - 1));
-  sub = sub < 0 ? 0 : (sub >= kNumSub ? kNumSub - 1 : sub);
+  int j, sub;
+  bucket_of(ql, &j, &sub);
   const int32_t pos = atomicAdd(&w.cursor[(cls * kNumJ + j) * kNumSub + sub], 1);
   w.order[pos] = k;
 }
@@ -145,7 +202,7 @@ __global__ void __launch_bounds__(kQueueThreads)
 // slots (one atomicAdd per warp per round), so neighbouring lanes get pairs
 // of nearly equal length.
 template <int R, bool PACKED, bool GRING>
-__global__ void __launch_bounds__(kLaneThreads)
+__global__ void __launch_bounds__(kLaneThreads, 4)
     k_lane(Batch b, Score sc, Work w, int cls, int j_lo, int j_hi, int head_id, int rs_log2,
            void* gring, int mparam) {
   using T = typename Ring<PACKED>::T;
@@ -167,20 +224,29 @@ __global__ void __launch_bounds__(kLaneThreads)
   const int32_t begin = w.seg_begin[cls * kNumJ + j_hi];
   const int32_t end = w.seg_end[cls * kNumJ + j_lo];
   int32_t* head = w.heads + head_id;
+  // rounds of 32 consecutive pairs per warp, all lanes together
   for (;;) {
-    const unsigned act = __activemask();
-    const int leader = __ffs(act) - 1;
     int32_t base = 0;
-    if (lane == leader) base = atomicAdd(head, __popc(act));
-    base = __shfl_sync(act, base, leader);
-    const int32_t idx = begin + base + __popc(act & ((1u << lane) - 1u));
-    if (idx >= end) break;
-    const int32_t k = w.order[idx];
-    const Pair pr = load_pair(b, k);
+    if (lane == 0) base = atomicAdd(head, 32);
+    base = begin + __shfl_sync(0xffffffffu, base, 0);
+    if (base >= end) break;
+    const int32_t idx = base + lane;
+    const bool valid = idx < end;
+    Pair pr;
+    int32_t k = 0;
+    if (valid) {
+      k = w.order[idx];
+      pr = load_pair(b, k);
+    } else {
+      pr.q = b.q_seq; pr.t = b.t_seq; pr.qlen = 0; pr.tlen = 0; pr.h0 = 1;
+    }
     Outcome o;
-    if (PACKED) o = lane_pair_p16<R>(pr, sc, s_prof, *reinterpret_cast<Ring<true>*>(&ring), mparam);
-    else o = lane_pair_i32<R>(pr, sc, s_prof, *reinterpret_cast<Ring<false>*>(&ring), mparam);
-    write_result(b, k, o.score, o.qle, o.tle, o.gscore, o.gtle, o.max_off, XT_OK, o.cells);
+    if (PACKED)
+      o = lane_pair_p16<R>(pr, valid, sc, s_prof, *reinterpret_cast<Ring<true>*>(&ring), mparam);
+    else
+      o = lane_pair_i32<R>(pr, valid, sc, s_prof, *reinterpret_cast<Ring<false>*>(&ring), mparam);
+    if (valid)
+      write_result(b, k, o.score, o.qle, o.tle, o.gscore, o.gtle, o.max_off, XT_OK, o.cells);
   }
 }
 
@@ -218,7 +284,7 @@ cudaError_t launch_classify(const Batch& b, const Score& sc, int32_t match, cons
 }
 
 cudaError_t launch_order(const Batch& b, const Work& w, cudaStream_t stream) {
-  k_scan<<<1, 32, 0, stream>>>(w);
+  k_scan<<<1, kScanThreads, 0, stream>>>(w);
   if (b.n > 0) {
     const int T = 256;
     k_scatter<<<(b.n + T - 1) / T, T, 0, stream>>>(b, w);

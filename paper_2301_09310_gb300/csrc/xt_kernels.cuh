@@ -21,7 +21,7 @@ constexpr uint8_t kJPacked = 2;          // bucket runs the one-lane engine: pac
 constexpr int kJMin = 5;                 // length buckets j: qlen + 2 <= 2^j
 constexpr int kJMax = 21;
 constexpr int kNumJ = kJMax + 1;
-constexpr int kNumSub = 8;               // sub-buckets (finer length order) per bucket
+constexpr int kNumSub = 256;             // sub-buckets per bucket: exact query length up to 2^9
 constexpr int kNumBuckets = kNumClasses * kNumJ * kNumSub;
 constexpr int kQueueThreads = 128;       // threads per CTA of the queue kernels
 constexpr int kMaxLaunches = 64;         // queue-kernel launches per call (heads)

@@ -95,10 +95,11 @@ __device__ __forceinline__ void lane_step_i32(int32_t (&Hl)[R], int32_t (&HAl)[R
   outF = upF;
 }
 
-// Extend one pair with one lane, 32-bit (requires h0 + match*min(qlen,tlen)
-// <= 32767 and qlen <= 65535 for the row key).
+// Extend the pairs of one warp, one pair per lane, 32-bit (requires h0 +
+// match*min(qlen,tlen) <= 32767 and qlen <= 65535 for the row key).  Lanes
+// walk their strips in lockstep, as in the packed form.
 template <int R>
-__device__ __forceinline__ Outcome lane_pair_i32(const Pair& pr, const Score& sc,
+__device__ __forceinline__ Outcome lane_pair_i32(const Pair& pr, bool valid, const Score& sc,
                                                  const uint32_t* s_prof, const Ring<false>& ring,
                                                  int32_t mc) {
   const int32_t qlen = pr.qlen, tlen = pr.tlen, h0 = pr.h0;
@@ -106,69 +107,86 @@ __device__ __forceinline__ Outcome lane_pair_i32(const Pair& pr, const Score& sc
   const uint32_t nnnn = sc.nnnn;
   RowState st;
   st.init(h0);
+  bool live = valid;
   int32_t hi_prev = -1;
-  for (int32_t i0 = 0; i0 < tlen; i0 += R) {
-    const int32_t rlast = min(tlen - 1, i0 + R - 1);
-    const int32_t lo = max(0, i0 - w);
-    const int32_t hi = min(qlen - 1, rlast + w);
-    if (lo > hi) break;
+  for (int32_t i0 = 0;; i0 += R) {
+    int32_t lo = 1, hi = 0, rlast = 0;
+    if (live) {
+      rlast = min(tlen - 1, i0 + R - 1);
+      lo = max(0, i0 - w);
+      hi = min(qlen - 1, rlast + w);
+      if (i0 >= tlen || lo > hi) live = false;
+    }
+    if (!__any_sync(0xffffffffu, live)) break;
     int32_t Hl[R], HAl[R], El[R], key[R];
     uint32_t sel[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int32_t i = i0 + r;
-      sel[r] = score_selector(i < tlen ? clamp_code(pr.t[i]) : 4u);
+      sel[r] = score_selector((live && i < tlen) ? clamp_code(pr.t[i]) : 4u);
       Hl[r] = (lo == 0 && i < tlen) ? col_m1(i, h0, sc) : 0;
       HAl[r] = Hl[r] - alpha;
       El[r] = 0;
       key[r] = -1;
     }
-    int32_t Hdiag;
+    int32_t Hdiag = 0;
     if (i0 == 0) Hdiag = h0;
     else if (lo == 0) Hdiag = col_m1(i0 - 1, h0, sc);
-    else Hdiag = ring.at(lo - 1).x;
-    for (int32_t c = lo; c <= hi; ++c) {
-      int32_t Hup, Fup;
-      if (i0 == 0) {
-        Hup = row_m1(c, h0, sc);
-        Fup = 0;
-      } else {
-        const int2 v = ring.at(c);
-        const bool ok = c <= hi_prev;
-        Hup = ok ? v.x : 0;
-        Fup = ok ? v.y : 0;
+    else if (live) Hdiag = ring.at(lo - 1).x;
+    const int32_t nsteps = live ? hi - lo + 1 : 0;
+    const int32_t nmax = __reduce_max_sync(0xffffffffu, nsteps);
+    const int32_t qlast = max(qlen - 1, 0);
+    uint32_t code_n = live ? clamp_code(__ldg(pr.q + min(lo + 1, qlast))) : 0u;
+    uint32_t prof_c = s_prof[live ? clamp_code(__ldg(pr.q + lo)) : 0u];
+    int2 ring_c = live ? ring.at(lo) : make_int2(0, 0);
+    for (int32_t s = 0; s < nmax; ++s) {
+      const int32_t c = lo + s;
+      const bool act = live && c <= hi;
+      const uint32_t code_nn = act ? clamp_code(__ldg(pr.q + min(c + 2, qlast))) : 0u;
+      const uint32_t prof_n = s_prof[code_n];
+      const int2 ring_n = act ? ring.at(c + 1) : make_int2(0, 0);
+      int32_t Hup = 0, Fup = 0;
+      if (act) {
+        if (i0 == 0) {
+          Hup = row_m1(c, h0, sc);
+        } else if (c <= hi_prev) {
+          Hup = ring_c.x;
+          Fup = ring_c.y;
+        }
       }
-      const uint32_t prof = s_prof[clamp_code(__ldg(pr.q + c))];
       const int32_t d0 = c - i0;
-      const bool body = (d0 >= R - 1 - w) && (d0 <= w) && (i0 + R <= tlen);
+      const bool body = act && (d0 >= R - 1 - w) && (d0 <= w) && (i0 + R <= tlen);
       int32_t oH, oF;
-      if (__all_sync(__activemask(), body)) {
-        lane_step_i32<R, false>(Hl, HAl, El, key, sel, prof, nnnn, Hdiag, Hup, Fup, c, alpha,
+      if (__all_sync(0xffffffffu, body || !live)) {
+        lane_step_i32<R, false>(Hl, HAl, El, key, sel, prof_c, nnnn, Hdiag, Hup, Fup, c, alpha,
                                 beta, mc, 0, R - 1, oH, oF);
-      } else {
-        lane_step_i32<R, true>(Hl, HAl, El, key, sel, prof, nnnn, Hdiag, Hup, Fup, c, alpha,
+      } else if (act) {
+        lane_step_i32<R, true>(Hl, HAl, El, key, sel, prof_c, nnnn, Hdiag, Hup, Fup, c, alpha,
                                beta, mc, d0 - w, min(d0 + w, tlen - 1 - i0), oH, oF);
       }
+      if (act) ring.at(c) = make_int2(oH, oF);
       Hdiag = Hup;
-      ring.at(c) = make_int2(oH, oF);
+      prof_c = prof_n;
+      code_n = code_nn;
+      ring_c = ring_n;
     }
     hi_prev = hi;
-    // rows in order; H(i, qlen-1) is the last column's H when the sweep reached it
-    int32_t last_m = 0;
+    if (live) {
+      int32_t last_m = 0;
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int32_t i = i0 + r;
-      if (i < tlen && !st.stop) {
-        const int32_t kv = key[r];
-        const int32_t m = kv < 0 ? 0 : (kv >> 16);
-        const int32_t mj = kv < 0 ? -1 : (kv & 0xFFFF);
-        const bool g_in = hi == qlen - 1 && (qlen - 1 - i <= w) && (i - (qlen - 1) <= w);
-        st.feed(i, m, mj, g_in ? Hl[r] : -1, sc);
-        last_m = m;
+      for (int r = 0; r < R; ++r) {
+        const int32_t i = i0 + r;
+        if (i < tlen && !st.stop) {
+          const int32_t kv = key[r];
+          const int32_t m = kv < 0 ? 0 : (kv >> 16);
+          const int32_t mj = kv < 0 ? -1 : (kv & 0xFFFF);
+          const bool g_in = hi == qlen - 1 && (qlen - 1 - i <= w) && (i - (qlen - 1) <= w);
+          st.feed(i, m, mj, g_in ? Hl[r] : -1, sc);
+          last_m = m;
+        }
       }
+      if (st.stop || (last_m == 0 && col_m1(rlast, h0, sc) == 0)) live = false;
     }
-    if (st.stop) break;
-    if (last_m == 0 && col_m1(rlast, h0, sc) == 0) break;
   }
   Outcome o;
   o.score = st.best; o.qle = st.bj + 1; o.tle = st.bi + 1; o.gscore = st.gscore;
@@ -178,30 +196,36 @@ __device__ __forceinline__ Outcome lane_pair_i32(const Pair& pr, const Score& sc
 }
 
 // ------------------------------------------------------------- packed lane
+// Row maximum in packed form: within blocks of kTagSteps = 32 steps each half
+// keeps key = H * 32 + (step within the block), so one packed max keeps the
+// largest H with the latest (largest) column; at the end of a block the keys
+// are folded into 32-bit (H << 16 | column) per row.  Needs H <= 1022.
+constexpr int kTagBits = 5;
+constexpr int kTagSteps = 1 << kTagBits;
+constexpr uint32_t kKeyNone = 0x80008000u;  // -32768 in both halves: no key yet
+
 // One step of the two stacked strips: the lower strip (low halves) at column
 // c, the upper strip (high halves) at column c - 1.  All values are packed
-// int16x2; H, E, F are >= 0 and bounded ((h0 + match*min(qlen,tlen) + 1) << k
-// <= 32767), so no half ever wraps.
+// int16x2; H, E, F are >= 0 and bounded, so no half ever wraps.
 //   MASKED: only rows lrlo..lrhi (lower) and hrlo..hrhi (upper) are in band;
-//           the others become dead and leave the row maximum alone.
-//   KEEP:   0 normal; 1 the upper strip has not started (its state is kept);
-//           2 the lower strip has finished (its state is kept).
+//           the others become dead and leave the row maximum alone; halves
+//           set in `keep` (a strip that has not started or has finished, or a
+//           lane with nothing to do this step) keep their state.
 // sel[r]: byte selector of row r in bits 0-15; bits 16-23 / 24-31 are 0xFF
 // when the lower / upper strip's target base is N (score n_score).
-// Mj[r]: column of the row maximum, lower strip in bits 0-15, upper in 16-31.
-template <int R, bool MASKED, bool HAS_N, int KEEP>
+template <int R, bool MASKED, bool HAS_N>
 __device__ __forceinline__ void lane_step_p16(uint32_t (&Hl)[R], uint32_t (&HAl)[R],
-                                              uint32_t (&El)[R], uint32_t (&Mx)[R],
-                                              uint32_t (&Mj)[R], const uint32_t (&sel)[R],
-                                              uint32_t prof_lo, uint32_t prof_hi, uint32_t nn2,
-                                              uint32_t D, uint32_t Hup, uint32_t Fup, uint32_t C2,
+                                              uint32_t (&El)[R], uint32_t (&K)[R],
+                                              const uint32_t (&sel)[R], uint32_t prof_lo,
+                                              uint32_t prof_hi, uint32_t nn2, uint32_t D,
+                                              uint32_t Hup, uint32_t Fup, uint32_t pos2,
                                               uint32_t na2, uint32_t nb2, uint32_t mcm,
                                               int32_t lrlo, int32_t lrhi, int32_t hrlo,
-                                              int32_t hrhi, uint32_t& outH, uint32_t& outF) {
+                                              int32_t hrhi, uint32_t keep, uint32_t& outH,
+                                              uint32_t& outF) {
   uint32_t upA = add16x2(Hup, na2);
   uint32_t upF = Fup;
   uint32_t upH = Hup;
-  constexpr uint32_t kKeepMask = KEEP == 1 ? 0xFFFF0000u : 0x0000FFFFu;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const uint32_t Hleft = Hl[r];
@@ -214,29 +238,24 @@ __device__ __forceinline__ void lane_step_p16(uint32_t (&Hl)[R], uint32_t (&HAl)
     uint32_t E = __viaddmax_s16x2_relu(El[r], nb2, HAl[r]);
     uint32_t F = __viaddmax_s16x2_relu(upF, nb2, upA);
     uint32_t H = __vimax3_s16x2(M, E, F);
-    bool inl = true, inh = true;
+    // H * 32 + step, both halves at once (halves >= 0, below 2^10: no carry)
+    uint32_t key = H * (uint32_t)kTagSteps + pos2;
     if (MASKED) {
-      inl = r >= lrlo && r <= lrhi;
-      inh = r >= hrlo && r <= hrhi;
+      const bool inl = r >= lrlo && r <= lrhi;
+      const bool inh = r >= hrlo && r <= hrhi;
       const uint32_t bm = (inl ? 0x0000FFFFu : 0u) | (inh ? 0xFFFF0000u : 0u);
       H &= bm;
       E &= bm;
       F &= bm;
+      key = (key & bm) | (kKeyNone & ~bm);
     }
-    bool ph, pl;
-    Mx[r] = __vibmax_s16x2(H, Mx[r], &ph, &pl);
-    if (MASKED) {
-      pl = pl && inl;
-      ph = ph && inh;
-    }
-    if (pl) Mj[r] = prmt(Mj[r], C2, 0x3254u);  // low half from C2
-    if (ph) Mj[r] = prmt(Mj[r], C2, 0x7610u);  // high half from C2
+    asm("max.s16x2 %0, %0, %1;" : "+r"(K[r]) : "r"(key));
     const uint32_t HA = add16x2(H, na2);
     D = Hleft;
-    if (KEEP) {
-      Hl[r] = (Hleft & kKeepMask) | (H & ~kKeepMask);
-      HAl[r] = (HAl[r] & kKeepMask) | (HA & ~kKeepMask);
-      El[r] = (El[r] & kKeepMask) | (E & ~kKeepMask);
+    if (MASKED) {
+      Hl[r] = (Hleft & keep) | (H & ~keep);
+      HAl[r] = (HAl[r] & keep) | (HA & ~keep);
+      El[r] = (El[r] & keep) | (E & ~keep);
     } else {
       Hl[r] = H; HAl[r] = HA; El[r] = E;
     }
@@ -246,11 +265,30 @@ __device__ __forceinline__ void lane_step_p16(uint32_t (&Hl)[R], uint32_t (&HAl)
   outF = upF;
 }
 
-// Extend one pair with one lane in packed 16-bit arithmetic.  mshift = k with
-// 2^k >= match + 1; the caller guarantees (h0 + match*min(qlen,tlen) + 1) << k
-// <= 32767 and qlen <= 65535.
+// Fold the block keys into the per-row (H << 16 | column) maxima; cbase is
+// the lower strip's column of block step 0 (the upper strip's is cbase - 1).
 template <int R>
-__device__ __forceinline__ Outcome lane_pair_p16(const Pair& pr, const Score& sc,
+__device__ __forceinline__ void fold_keys(uint32_t (&K)[R], int32_t (&Blo)[R], int32_t (&Bhi)[R],
+                                          int32_t cbase) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int32_t kl = lo16(K[r]), kh = hi16(K[r]);
+    if (kl >= 0) Blo[r] = max(Blo[r], ((kl >> kTagBits) << 16) | (cbase + (kl & (kTagSteps - 1))));
+    if (kh >= 0)
+      Bhi[r] = max(Bhi[r], ((kh >> kTagBits) << 16) | (cbase - 1 + (kh & (kTagSteps - 1))));
+    K[r] = kKeyNone;
+  }
+}
+
+// Extend the pairs of one warp, one pair per lane, in packed 16-bit
+// arithmetic.  The lanes walk their strips in lockstep (the batch is ordered
+// by exact query length, so the 32 pairs of a warp share one geometry) and a
+// lane whose pair is done, or has no pair (valid = false), idles masked.
+// mshift = k with 2^k >= match + 1.  The caller guarantees, with B = h0 +
+// match*min(qlen,tlen): (B + 1) << k <= 32767, B * 32 + 31 <= 32767,
+// 1 <= qlen <= 65535 and tlen >= 1.
+template <int R>
+__device__ __forceinline__ Outcome lane_pair_p16(const Pair& pr, bool valid, const Score& sc,
                                                  const uint32_t* s_prof, const Ring<true>& ring,
                                                  int mshift) {
   const int32_t qlen = pr.qlen, tlen = pr.tlen, h0 = pr.h0;
@@ -261,21 +299,28 @@ __device__ __forceinline__ Outcome lane_pair_p16(const Pair& pr, const Score& sc
   // halves are >= 0 and below 2^(15-k): a 32-bit multiply by 2^k shifts each half
   const uint32_t mcm = 1u << mshift;
   constexpr int RR = 2 * R;
+  constexpr int32_t kFar = 1 << 30;
   RowState st;
   st.init(h0);
+  bool live = valid;
   int32_t hi_prev = -1;
-  for (int32_t i0 = 0; i0 < tlen; i0 += RR) {
-    const int32_t rlast = min(tlen - 1, i0 + RR - 1);
-    const int32_t lo = max(0, i0 - w);
-    const int32_t hi = min(qlen - 1, rlast + w);
-    if (lo > hi) break;
-    uint32_t Hl[R], HAl[R], El[R], Mx[R], sel[R], Mj[R];
+  for (int32_t i0 = 0;; i0 += RR) {
+    int32_t lo = 1, hi = 0, rlast = 0;
+    if (live) {
+      rlast = min(tlen - 1, i0 + RR - 1);
+      lo = max(0, i0 - w);
+      hi = min(qlen - 1, rlast + w);
+      if (i0 >= tlen || lo > hi) live = false;
+    }
+    if (!__any_sync(0xffffffffu, live)) break;
+    uint32_t Hl[R], HAl[R], El[R], K[R], sel[R];
+    int32_t Blo[R], Bhi[R];
     uint32_t anyN = 0;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int32_t il = i0 + r, ih = i0 + R + r;
-      const uint32_t cl = il < tlen ? clamp_code(pr.t[il]) : 0u;
-      const uint32_t ch = ih < tlen ? clamp_code(pr.t[ih]) : 0u;
+      const uint32_t cl = (live && il < tlen) ? clamp_code(pr.t[il]) : 0u;
+      const uint32_t ch = (live && ih < tlen) ? clamp_code(pr.t[ih]) : 0u;
       const uint32_t bl = cl & 3u, bh = 4u + (ch & 3u);
       const uint32_t nf = (cl == 4u ? 0x00FF0000u : 0u) | (ch == 4u ? 0xFF000000u : 0u);
       sel[r] = bl | ((bl | 8u) << 4) | (bh << 8) | ((bh | 8u) << 12) | nf;
@@ -286,109 +331,123 @@ __device__ __forceinline__ Outcome lane_pair_p16(const Pair& pr, const Score& sc
       Hl[r] = pack16(hl, hh);
       HAl[r] = add16x2(Hl[r], na2);
       El[r] = 0;
-      Mx[r] = 0;
-      Mj[r] = 0xFFFFFFFFu;  // -1 in both halves: no column yet
+      K[r] = kKeyNone;
+      Blo[r] = -1;
+      Bhi[r] = -1;
     }
-    const bool has_n = __any_sync(__activemask(), anyN != 0);
+    const bool has_n = __any_sync(0xffffffffu, anyN != 0);
     // lower strip's diagonal at its first column: H(i0-1, lo-1)
-    int32_t dlo;
+    int32_t dlo = 0;
     if (i0 == 0) dlo = h0;
     else if (lo == 0) dlo = col_m1(i0 - 1, h0, sc);
-    else dlo = lo16(ring.at(lo - 1));
-    // lower strip's bottom row (row i0+R-1) at the previous column and the one
-    // before; at column lo - 1 it is the left boundary
+    else if (live) dlo = lo16(ring.at(lo - 1));
+    // lower strip's bottom row (row i0+R-1) at column lo - 1: the left boundary
     const int32_t lb = (lo == 0 && i0 + R - 1 < tlen) ? col_m1(i0 + R - 1, h0, sc) : 0;
-    int32_t botH1 = lb, botF1 = lb, botH2 = lb;
+    uint32_t oH1 = (uint32_t)lb, oF1 = (uint32_t)lb, oH2 = (uint32_t)lb;  // low halves used
+    uint32_t tHF_prev = (uint32_t)dlo & 0xFFFFu;
     uint32_t prof_prev = 0;
-    const int32_t nsteps = hi - lo + 2;
+    // steps: s = 0 .. nsteps-1 (lower strip at lo + s, upper at lo + s - 1); the
+    // unmasked range is where both strips are active and every row is in band
+    const int32_t nsteps = live ? hi - lo + 2 : 0;
+    int32_t sb_lo = 0, sb_hi = kFar;
+    if (live) {
+      sb_lo = max(1, RR - w + i0 - lo);
+      sb_hi = min(hi - lo, w + i0 - lo);
+      if (i0 + RR > tlen) sb_hi = -1;
+    }
+    const int32_t nmax = __reduce_max_sync(0xffffffffu, nsteps);
+    const int32_t fs = (int32_t)__reduce_max_sync(0xffffffffu, (uint32_t)sb_lo);
+    const int32_t fe = min(__reduce_min_sync(0xffffffffu, sb_hi), nmax - 1);
     // software pipeline: query codes two columns ahead, profile and ring one ahead
     const int32_t qlast = qlen - 1;
-    uint32_t code_n = clamp_code(__ldg(pr.q + min(lo + 1, qlast)));
-    uint32_t prof_c = s_prof[clamp_code(__ldg(pr.q + lo))];
-    uint32_t ring_c = ring.at(lo);
-    for (int32_t s = 0; s < nsteps; ++s) {
-      const int32_t c = lo + s;  // lower strip column; the upper strip is at c - 1
-      const bool lo_act = c <= hi;
-      const bool hi_act = s >= 1;
-      // issue the next step's loads first
-      const uint32_t code_nn = clamp_code(__ldg(pr.q + min(c + 2, qlast)));
+    const uint8_t* qp = pr.q;
+    uint32_t code_n = live ? clamp_code(__ldg(qp + min(lo + 1, qlast))) : 0u;
+    uint32_t prof_c = s_prof[live ? clamp_code(__ldg(qp + lo)) : 0u];
+    uint32_t ring_c = live ? ring.at(lo) : 0u;
+    int32_t blk = 0;     // steps taken in the current key block
+    int32_t cbase = lo;  // lower strip's column at block step 0
+    auto step = [&](int32_t s, int mode) {
+      const int32_t c = lo + s;
+      const bool lo_act = live && c <= hi;
+      const bool hi_act = live && s >= 1 && c - 1 <= hi;
+      const uint32_t code_nn = lo_act ? clamp_code(__ldg(qp + min(c + 2, qlast))) : 0u;
       const uint32_t prof_n = s_prof[code_n];
-      const uint32_t ring_n = ring.at(c + 1);
-      int32_t tH = 0, tF = 0;  // row above the lower strip at column c
-      if (lo_act) {
-        if (i0 == 0) {
-          tH = row_m1(c, h0, sc);
-        } else if (c <= hi_prev) {
-          tH = lo16(ring_c);
-          tF = hi16(ring_c);
-        }
-      }
+      const uint32_t ring_n = lo_act ? ring.at(c + 1) : 0u;
+      // (H, F) of the row above at column c: row -1 on the first strip, else the
+      // previous strip's bottom row (dead where it never reached)
+      uint32_t tHF;
+      if (i0 == 0) tHF = lo_act ? ((uint32_t)row_m1(c, h0, sc) & 0xFFFFu) : 0u;
+      else tHF = (lo_act && c <= hi_prev) ? ring_c : 0u;
       const uint32_t prof = lo_act ? prof_c : 0u;
-      const uint32_t Hup = pack16(tH, botH1);
-      const uint32_t Fup = pack16(tF, botF1);
-      const uint32_t D = pack16(dlo, botH2);
-      const uint32_t C2 = pack16(c, c - 1);
-      const int32_t d0 = c - i0;
-      const bool body = lo_act && hi_act && d0 >= RR - w && d0 <= w && i0 + RR <= tlen;
+      const uint32_t Hup = prmt(tHF, oH1, 0x5410u);
+      const uint32_t Fup = prmt(tHF, oF1, 0x5432u);
+      const uint32_t D = prmt(tHF_prev, oH2, 0x5410u);
+      const uint32_t pos2 = (uint32_t)blk * 0x00010001u;
       uint32_t oH, oF;
-      if (__all_sync(__activemask(), body)) {
+      if (mode == 0) {
         if (has_n)
-          lane_step_p16<R, false, true, 0>(Hl, HAl, El, Mx, Mj, sel, prof, prof_prev, nn2, D,
-                                           Hup, Fup, C2, na2, nb2, mcm, 0, R - 1, 0, R - 1, oH,
-                                           oF);
+          lane_step_p16<R, false, true>(Hl, HAl, El, K, sel, prof, prof_prev, nn2, D, Hup, Fup,
+                                        pos2, na2, nb2, mcm, 0, R - 1, 0, R - 1, 0u, oH, oF);
         else
-          lane_step_p16<R, false, false, 0>(Hl, HAl, El, Mx, Mj, sel, prof, prof_prev, nn2, D,
-                                            Hup, Fup, C2, na2, nb2, mcm, 0, R - 1, 0, R - 1, oH,
-                                            oF);
+          lane_step_p16<R, false, false>(Hl, HAl, El, K, sel, prof, prof_prev, nn2, D, Hup, Fup,
+                                         pos2, na2, nb2, mcm, 0, R - 1, 0, R - 1, 0u, oH, oF);
       } else {
-        // in-band rows: |i - col| <= w and i < tlen, for an active strip only
+        const int32_t d0 = c - i0;
         const int32_t lrlo = lo_act ? d0 - w : R;
         const int32_t lrhi = lo_act ? min(d0 + w, tlen - 1 - i0) : -1;
         const int32_t dh = d0 - 1 - R;  // upper strip: column c-1 minus its first row
         const int32_t hrlo = hi_act ? dh - w : R;
         const int32_t hrhi = hi_act ? min(dh + w, tlen - 1 - i0 - R) : -1;
-        if (s == 0)
-          lane_step_p16<R, true, true, 1>(Hl, HAl, El, Mx, Mj, sel, prof, prof_prev, nn2, D, Hup,
-                                          Fup, C2, na2, nb2, mcm, lrlo, lrhi, hrlo, hrhi, oH, oF);
-        else if (!lo_act)
-          lane_step_p16<R, true, true, 2>(Hl, HAl, El, Mx, Mj, sel, prof, prof_prev, nn2, D, Hup,
-                                          Fup, C2, na2, nb2, mcm, lrlo, lrhi, hrlo, hrhi, oH, oF);
-        else
-          lane_step_p16<R, true, true, 0>(Hl, HAl, El, Mx, Mj, sel, prof, prof_prev, nn2, D, Hup,
-                                          Fup, C2, na2, nb2, mcm, lrlo, lrhi, hrlo, hrhi, oH, oF);
+        const uint32_t keep = (lo_act ? 0u : 0x0000FFFFu) | (hi_act ? 0u : 0xFFFF0000u);
+        lane_step_p16<R, true, true>(Hl, HAl, El, K, sel, prof, prof_prev, nn2, D, Hup, Fup, pos2,
+                                     na2, nb2, mcm, lrlo, lrhi, hrlo, hrhi, keep, oH, oF);
       }
-      if (hi_act) ring.at(c - 1) = (oH >> 16) | (oF & 0xFFFF0000u);
-      botH2 = botH1;
-      botH1 = lo16(oH);
-      botF1 = lo16(oF);
-      dlo = tH;
+      if (hi_act) ring.at(c - 1) = prmt(oH, oF, 0x7632u);
+      oH2 = oH1;
+      oH1 = oH;
+      oF1 = oF;
+      tHF_prev = tHF;
       prof_prev = prof;
       prof_c = prof_n;
       code_n = code_nn;
       ring_c = ring_n;
+      if (++blk == kTagSteps) {
+        fold_keys<R>(K, Blo, Bhi, cbase);
+        cbase += kTagSteps;
+        blk = 0;
+      }
+    };
+    int32_t s = 0;
+    if (fs <= fe) {
+      for (; s < fs; ++s) step(s, 1);
+      for (; s <= fe; ++s) step(s, 0);
     }
+    for (; s < nmax; ++s) step(s, 1);
+    fold_keys<R>(K, Blo, Bhi, cbase);
     hi_prev = hi;
-    int32_t last_m = 0;
-    const bool reach = hi == qlen - 1;
+    if (live) {
+      int32_t last_m = 0;
+      const bool reach = hi == qlen - 1;
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
+      for (int half = 0; half < 2; ++half) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int32_t i = i0 + half * R + r;
-        if (i < tlen && !st.stop) {
-          const int32_t m = half ? hi16(Mx[r]) : lo16(Mx[r]);
-          const int32_t mj = half ? hi16(Mj[r]) : lo16(Mj[r]);
-          // after the sweep, Hl holds H(i, hi) of both strips (each strip kept
-          // its state once it had passed column hi)
-          const bool g_in = reach && (qlen - 1 - i <= w) && (i - (qlen - 1) <= w);
-          const int32_t g = g_in ? (half ? hi16(Hl[r]) : lo16(Hl[r])) : -1;
-          st.feed(i, m, mj, g, sc);
-          last_m = m;
+        for (int r = 0; r < R; ++r) {
+          const int32_t i = i0 + half * R + r;
+          if (i < tlen && !st.stop) {
+            const int32_t bk = half ? Bhi[r] : Blo[r];
+            const int32_t m = bk < 0 ? 0 : (bk >> 16);
+            const int32_t mj = bk < 0 ? -1 : (bk & 0xFFFF);
+            // after the sweep, Hl holds H(i, hi) of both strips (each strip kept
+            // its state once it had passed column hi)
+            const bool g_in = reach && (qlen - 1 - i <= w) && (i - (qlen - 1) <= w);
+            const int32_t g = g_in ? (half ? hi16(Hl[r]) : lo16(Hl[r])) : -1;
+            st.feed(i, m, mj, g, sc);
+            last_m = m;
+          }
         }
       }
+      if (st.stop || (last_m == 0 && col_m1(rlast, h0, sc) == 0)) live = false;
     }
-    if (st.stop) break;
-    if (last_m == 0 && col_m1(rlast, h0, sc) == 0) break;
   }
   Outcome o;
   o.score = st.best; o.qle = st.bj + 1; o.tle = st.bi + 1; o.gscore = st.gscore;
