@@ -198,12 +198,13 @@ bool lane_launch(xt_ctx* ctx, const Score& sc, int cls, int j, bool allow_gring,
   const int rows = cls == CLS_PACKED ? 2 * R : R;
   const int64_t need = std::min<int64_t>((int64_t)1 << j, next_pow2(rows + 2 * (int64_t)sc.w + 2));
   const int lg = log2_ceil(need);
-  const size_t smem = (size_t)kLaneThreads * lane_ring_bytes(cls, lg);
-  const bool gring = smem > kLaneSmemCap;
+  const size_t ring = (size_t)kLaneThreads * lane_ring_bytes(cls, lg);
+  const bool gring = ring > kLaneSmemCap;
   if (gring && !allow_gring) return false;
   L->cls = cls; L->j_lo = j; L->j_hi = j; L->lane = true; L->P = 1; L->R = R;
   L->rs_log2 = lg; L->global_ring = gring; L->slab = gring ? ((int64_t)1 << lg) : 0;
-  const int per_sm = gring ? 4 : (int)std::max<size_t>(1, std::min<size_t>(8, (size_t)(200 * 1024) / (smem + 1024)));
+  const size_t smem = (gring ? 0 : ring) + (cls == CLS_PACKED ? lane_stage_bytes(j) : 0);
+  const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (size_t)(220 * 1024) / (smem + 1024)));
   L->grid = ctx->num_sms * per_sm;
   int k = 0;
   while ((1 << k) < ctx->match + 1) ++k;

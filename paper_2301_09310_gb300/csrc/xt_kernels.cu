@@ -62,8 +62,8 @@ __global__ void k_classify(Batch b, Score sc, int32_t match, int32_t mshift, JFl
   const bool wide = bound > 32767 || ql > 65535;
   const uint8_t jf = jfl.f[j];
   int cls = wide ? CLS_WIDE : CLS_NARROW;
-  // packed: the anchoring multiply and the 16-bit row keys (H * 32 + step) fit
-  if (!wide && (jf & kJPacked) && ((bound + 1) << mshift) <= 32767 && bound * 32 + 31 <= 32767)
+  // packed: the anchoring multiply and the 16-bit row keys (H * 64 + step) fit
+  if (!wide && (jf & kJPacked) && ((bound + 1) << mshift) <= 32767 && bound * 64 + 63 <= 32767)
     cls = CLS_PACKED;
   if (jf & kJHuge) cls = CLS_HUGE;
   w.pclass[k] = (uint8_t)cls;
@@ -201,26 +201,32 @@ __global__ void __launch_bounds__(kQueueThreads)
 // Every lane extends whole pairs on its own; the warp takes consecutive queue
 // slots (one atomicAdd per warp per round), so neighbouring lanes get pairs
 // of nearly equal length.
-template <int R, bool PACKED, bool GRING>
+template <int R, bool PACKED, bool GRING, bool QSTAGE>
 __global__ void __launch_bounds__(kLaneThreads, 4)
     k_lane(Batch b, Score sc, Work w, int cls, int j_lo, int j_hi, int head_id, int rs_log2,
-           void* gring, int mparam) {
+           void* gring, int mparam, int qs_log2) {
   using T = typename Ring<PACKED>::T;
   extern __shared__ __align__(16) unsigned char s_dyn[];
   __shared__ uint32_t s_prof[8];
   if (threadIdx.x < 5) s_prof[threadIdx.x] = sc.prof[threadIdx.x];
   __syncthreads();
   const int lane = threadIdx.x & 31;
+  // ring: column c of lane t at [(c & mask) * kLaneThreads + t], so the lanes
+  // of a warp (which sit on the same column) touch consecutive words
   Ring<PACKED> ring;
   ring.mask = (1 << rs_log2) - 1;
+  ring.stride = kLaneThreads;
+  size_t ring_bytes = 0;
   if (GRING) {
     ring.base = reinterpret_cast<T*>(gring) +
-                ((int64_t)blockIdx.x * kLaneThreads + threadIdx.x) * ((int64_t)1 << rs_log2);
-    ring.stride = 1;
+                (int64_t)blockIdx.x * kLaneThreads * ((int64_t)1 << rs_log2) + threadIdx.x;
   } else {
     ring.base = reinterpret_cast<T*>(s_dyn) + threadIdx.x;
-    ring.stride = kLaneThreads;
+    ring_bytes = (size_t)kLaneThreads * ((size_t)1 << rs_log2) * sizeof(T);
   }
+  Query<QSTAGE> qs;
+  qs.stage = QSTAGE ? s_dyn + ring_bytes + (size_t)(threadIdx.x >> 5) * (32u << qs_log2) + lane
+                    : nullptr;
   const int32_t begin = w.seg_begin[cls * kNumJ + j_hi];
   const int32_t end = w.seg_end[cls * kNumJ + j_lo];
   int32_t* head = w.heads + head_id;
@@ -241,8 +247,10 @@ __global__ void __launch_bounds__(kLaneThreads, 4)
       pr.q = b.q_seq; pr.t = b.t_seq; pr.qlen = 0; pr.tlen = 0; pr.h0 = 1;
     }
     Outcome o;
+    qs.g = pr.q;
     if (PACKED)
-      o = lane_pair_p16<R>(pr, valid, sc, s_prof, *reinterpret_cast<Ring<true>*>(&ring), mparam);
+      o = lane_pair_p16<R, QSTAGE>(pr, valid, sc, s_prof, *reinterpret_cast<Ring<true>*>(&ring),
+                                   mparam, qs);
     else
       o = lane_pair_i32<R>(pr, valid, sc, s_prof, *reinterpret_cast<Ring<false>*>(&ring), mparam);
     if (valid)
@@ -334,34 +342,51 @@ size_t lane_ring_bytes(int cls, int rs_log2) {
   return ((size_t)1 << rs_log2) * (cls == CLS_PACKED ? sizeof(uint32_t) : sizeof(int2));
 }
 
-template <int R, bool PACKED, bool GRING>
+size_t lane_stage_bytes(int j_hi) {
+  return j_hi <= kLaneStageJMax ? (size_t)kLaneThreads << j_hi : 0;
+}
+
+template <int R, bool PACKED, bool GRING, bool QSTAGE>
 static cudaError_t launch_lane_t(const Batch& b, const Score& sc, const Work& w, const Launch& L,
                                  int head_id, void* gring, cudaStream_t stream) {
-  const size_t smem = GRING ? 0 : kLaneThreads * lane_ring_bytes(L.cls, L.rs_log2);
-  auto kern = k_lane<R, PACKED, GRING>;
+  const size_t smem = (GRING ? 0 : kLaneThreads * lane_ring_bytes(L.cls, L.rs_log2)) +
+                      (QSTAGE ? lane_stage_bytes(L.j_hi) : 0);
+  auto kern = k_lane<R, PACKED, GRING, QSTAGE>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
   kern<<<L.grid, kLaneThreads, smem, stream>>>(b, sc, w, L.cls, L.j_lo, L.j_hi, head_id,
-                                               L.rs_log2, gring, L.mparam);
+                                               L.rs_log2, gring, L.mparam, L.j_hi);
   return cudaGetLastError();
 }
 
 cudaError_t launch_lane(const Batch& b, const Score& sc, const Work& w, const Launch& L,
                         int head_id, void* gring, cudaStream_t stream) {
   const bool packed = L.cls == CLS_PACKED;
-#define XT_L(RR)                                                                         \
-  if (L.R == RR) {                                                                       \
-    if (packed)                                                                          \
-      return L.global_ring ? launch_lane_t<RR, true, true>(b, sc, w, L, head_id, gring, stream) \
-                           : launch_lane_t<RR, true, false>(b, sc, w, L, head_id, gring, stream); \
-    return L.global_ring ? launch_lane_t<RR, false, true>(b, sc, w, L, head_id, gring, stream) \
-                         : launch_lane_t<RR, false, false>(b, sc, w, L, head_id, gring, stream); \
+  const bool stage = packed && lane_stage_bytes(L.j_hi) > 0;
+#define XT_LG(RR, PK, GR)                                                                       \
+  return stage ? launch_lane_t<RR, PK, GR, true>(b, sc, w, L, head_id, gring, stream)           \
+               : launch_lane_t<RR, PK, GR, false>(b, sc, w, L, head_id, gring, stream);
+#define XT_L(RR)                                                                                \
+  if (L.R == RR) {                                                                              \
+    if (packed) {                                                                               \
+      if (L.global_ring) { XT_LG(RR, true, true) } else { XT_LG(RR, true, false) }             \
+    }                                                                                           \
+    return L.global_ring ? launch_lane_t<RR, false, true, false>(b, sc, w, L, head_id, gring, stream) \
+                         : launch_lane_t<RR, false, false, false>(b, sc, w, L, head_id, gring, stream); \
   }
-  XT_L(4) XT_L(8) XT_L(16)
+  XT_L(4) XT_L(8)
+  if (L.R == 16) {
+    if (packed)
+      return L.global_ring ? launch_lane_t<16, true, true, false>(b, sc, w, L, head_id, gring, stream)
+                           : launch_lane_t<16, true, false, false>(b, sc, w, L, head_id, gring, stream);
+    return L.global_ring ? launch_lane_t<16, false, true, false>(b, sc, w, L, head_id, gring, stream)
+                         : launch_lane_t<16, false, false, false>(b, sc, w, L, head_id, gring, stream);
+  }
 #undef XT_L
+#undef XT_LG
   return cudaErrorInvalidValue;
 }
 

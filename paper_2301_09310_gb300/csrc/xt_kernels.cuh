@@ -38,6 +38,7 @@ struct Work {
 };
 
 constexpr int kLaneThreads = 128;        // threads per CTA of the one-lane kernels
+constexpr int kLaneStageJMax = 9;        // one-lane kernels stage queries up to 2^9 - 2 bases
 
 // One persistent launch: pairs of class cls, buckets [j_lo, j_hi].
 struct Launch {
@@ -69,6 +70,8 @@ cudaError_t launch_lane(const Batch& b, const Score& sc, const Work& w, const La
 size_t queue_smem_bytes(int P, int rs_log2);
 // Ring bytes per lane of a one-lane launch (per CTA in shared memory: x kLaneThreads).
 size_t lane_ring_bytes(int cls, int rs_log2);
+// Query staging bytes per CTA of a one-lane launch whose longest bucket is j_hi (0: none).
+size_t lane_stage_bytes(int j_hi);
 int max_smem_per_block_optin(int device);
 
 }  // namespace xt

@@ -58,6 +58,23 @@ struct Ring {
   __device__ __forceinline__ T& at(int32_t c) const { return base[(c & mask) * stride]; }
 };
 
+// Query codes of one pair: read from global memory, or from a copy staged in
+// shared memory (byte c of the lane at stage[c * 32], lanes of a warp
+// interleaved so that a warp reading one column hits 32 consecutive bytes).
+template <bool STAGED>
+struct Query {
+  const uint8_t* g;  // global query
+  uint8_t* stage;    // this lane's column 0 in the warp's stage
+  __device__ __forceinline__ void load(int32_t qlen, bool live) {
+    if (STAGED && live)
+      for (int32_t c = 0; c < qlen; ++c) stage[c * 32] = (uint8_t)clamp_code(__ldg(g + c));
+  }
+  __device__ __forceinline__ uint32_t code(int32_t c) const {
+    if (STAGED) return stage[c * 32];
+    return clamp_code(__ldg(g + c));
+  }
+};
+
 // ----------------------------------------------------------- 32-bit lane
 template <int R, bool MASKED>
 __device__ __forceinline__ void lane_step_i32(int32_t (&Hl)[R], int32_t (&HAl)[R],
@@ -196,32 +213,35 @@ __device__ __forceinline__ Outcome lane_pair_i32(const Pair& pr, bool valid, con
 }
 
 // ------------------------------------------------------------- packed lane
-// Row maximum in packed form: within blocks of kTagSteps = 32 steps each half
-// keeps key = H * 32 + (step within the block), so one packed max keeps the
+// Row maximum in packed form: within blocks of kTagSteps = 64 steps each half
+// keeps key = H * 64 + (step within the block), so one packed max keeps the
 // largest H with the latest (largest) column; at the end of a block the keys
-// are folded into 32-bit (H << 16 | column) per row.  Needs H <= 1022.
-constexpr int kTagBits = 5;
+// are folded into 32-bit (H << 16 | column) per row.  Needs H <= 510.
+constexpr int kTagBits = 6;
 constexpr int kTagSteps = 1 << kTagBits;
 constexpr uint32_t kKeyNone = 0x80008000u;  // -32768 in both halves: no key yet
 
 // One step of the two stacked strips: the lower strip (low halves) at column
 // c, the upper strip (high halves) at column c - 1.  All values are packed
 // int16x2; H, E, F are >= 0 and bounded, so no half ever wraps.
-//   MASKED: only rows lrlo..lrhi (lower) and hrlo..hrhi (upper) are in band;
-//           the others become dead and leave the row maximum alone; halves
-//           set in `keep` (a strip that has not started or has finished, or a
-//           lane with nothing to do this step) keep their state.
+//   MASKED: bit r (lower strip) / bit 16 + r (upper strip) of `inband` says
+//     whether row r's cell is in band.  An out-of-band cell gets H = F = 0:
+//     that is all its in-band neighbours can read (E of a cell left of the
+//     band is rebuilt from a dead H; E of a cell right of it only flows
+//     further right).  Its row key may move, but only to H = 0, and a row
+//     whose maximum is 0 takes its column from the band geometry instead.
+//   KEEP: halves set in `keep` (a strip that has not started, or has
+//     finished) keep their state.
 // sel[r]: byte selector of row r in bits 0-15; bits 16-23 / 24-31 are 0xFF
 // when the lower / upper strip's target base is N (score n_score).
-template <int R, bool MASKED, bool HAS_N>
+template <int R, bool MASKED, bool HAS_N, bool KEEP>
 __device__ __forceinline__ void lane_step_p16(uint32_t (&Hl)[R], uint32_t (&HAl)[R],
                                               uint32_t (&El)[R], uint32_t (&K)[R],
                                               const uint32_t (&sel)[R], uint32_t prof_lo,
                                               uint32_t prof_hi, uint32_t nn2, uint32_t D,
                                               uint32_t Hup, uint32_t Fup, uint32_t pos2,
                                               uint32_t na2, uint32_t nb2, uint32_t mcm,
-                                              int32_t lrlo, int32_t lrhi, int32_t hrlo,
-                                              int32_t hrhi, uint32_t keep, uint32_t& outH,
+                                              uint32_t inband, uint32_t keep, uint32_t& outH,
                                               uint32_t& outF) {
   uint32_t upA = add16x2(Hup, na2);
   uint32_t upF = Fup;
@@ -235,24 +255,20 @@ __device__ __forceinline__ void lane_step_p16(uint32_t (&Hl)[R], uint32_t (&HAl)
       S = (S & ~nm) | (nn2 & nm);
     }
     const uint32_t M = __viaddmin_s16x2(D, S, D * mcm);
-    uint32_t E = __viaddmax_s16x2_relu(El[r], nb2, HAl[r]);
+    const uint32_t E = __viaddmax_s16x2_relu(El[r], nb2, HAl[r]);
     uint32_t F = __viaddmax_s16x2_relu(upF, nb2, upA);
     uint32_t H = __vimax3_s16x2(M, E, F);
-    // H * 32 + step, both halves at once (halves >= 0, below 2^10: no carry)
-    uint32_t key = H * (uint32_t)kTagSteps + pos2;
     if (MASKED) {
-      const bool inl = r >= lrlo && r <= lrhi;
-      const bool inh = r >= hrlo && r <= hrhi;
-      const uint32_t bm = (inl ? 0x0000FFFFu : 0u) | (inh ? 0xFFFF0000u : 0u);
+      // bits r and 16 + r moved to the sign bits of bytes 1 and 3, then spread
+      const uint32_t bm = prmt(inband << (15 - r), 0u, 0xBB99u);
       H &= bm;
-      E &= bm;
       F &= bm;
-      key = (key & bm) | (kKeyNone & ~bm);
     }
-    asm("max.s16x2 %0, %0, %1;" : "+r"(K[r]) : "r"(key));
+    // H * 64 + step, both halves at once (halves >= 0, below 2^9: no carry)
+    asm("max.s16x2 %0, %0, %1;" : "+r"(K[r]) : "r"(H * (uint32_t)kTagSteps + pos2));
     const uint32_t HA = add16x2(H, na2);
     D = Hleft;
-    if (MASKED) {
+    if (KEEP) {
       Hl[r] = (Hleft & keep) | (H & ~keep);
       HAl[r] = (HAl[r] & keep) | (HA & ~keep);
       El[r] = (El[r] & keep) | (E & ~keep);
@@ -263,6 +279,14 @@ __device__ __forceinline__ void lane_step_p16(uint32_t (&Hl)[R], uint32_t (&HAl)
   }
   outH = upH;
   outF = upF;
+}
+
+// Bits lo..hi (clamped to 0..n-1) set; 0 when the range is empty.
+__device__ __forceinline__ uint32_t bit_range(int32_t lo, int32_t hi, int n) {
+  lo = max(lo, 0);
+  hi = min(hi, n - 1);
+  if (lo > hi) return 0u;
+  return ((2u << hi) - 1u) & ~((1u << lo) - 1u);
 }
 
 // Fold the block keys into the per-row (H << 16 | column) maxima; cbase is
@@ -287,10 +311,10 @@ __device__ __forceinline__ void fold_keys(uint32_t (&K)[R], int32_t (&Blo)[R], i
 // mshift = k with 2^k >= match + 1.  The caller guarantees, with B = h0 +
 // match*min(qlen,tlen): (B + 1) << k <= 32767, B * 32 + 31 <= 32767,
 // 1 <= qlen <= 65535 and tlen >= 1.
-template <int R>
+template <int R, bool STAGED>
 __device__ __forceinline__ Outcome lane_pair_p16(const Pair& pr, bool valid, const Score& sc,
                                                  const uint32_t* s_prof, const Ring<true>& ring,
-                                                 int mshift) {
+                                                 int mshift, Query<STAGED> qs) {
   const int32_t qlen = pr.qlen, tlen = pr.tlen, h0 = pr.h0;
   const int32_t alpha = sc.alpha, beta = sc.beta, w = sc.w;
   const uint32_t na2 = pack16(-alpha, -alpha), nb2 = pack16(-beta, -beta);
@@ -303,6 +327,7 @@ __device__ __forceinline__ Outcome lane_pair_p16(const Pair& pr, bool valid, con
   RowState st;
   st.init(h0);
   bool live = valid;
+  qs.load(qlen, live);
   int32_t hi_prev = -1;
   for (int32_t i0 = 0;; i0 += RR) {
     int32_t lo = 1, hi = 0, rlast = 0;
@@ -358,21 +383,26 @@ __device__ __forceinline__ Outcome lane_pair_p16(const Pair& pr, bool valid, con
     const int32_t nmax = __reduce_max_sync(0xffffffffu, nsteps);
     const int32_t fs = (int32_t)__reduce_max_sync(0xffffffffu, (uint32_t)sb_lo);
     const int32_t fe = min(__reduce_min_sync(0xffffffffu, sb_hi), nmax - 1);
-    // software pipeline: query codes two columns ahead, profile and ring one ahead
+    // software pipeline: ring entries and query codes three columns ahead,
+    // profiles one ahead (the ring row of the previous strip is usually an
+    // L2 hit by now, so one step of lead time is not enough)
     const int32_t qlast = qlen - 1;
-    const uint8_t* qp = pr.q;
-    uint32_t code_n = live ? clamp_code(__ldg(qp + min(lo + 1, qlast))) : 0u;
-    uint32_t prof_c = s_prof[live ? clamp_code(__ldg(qp + lo)) : 0u];
+    uint32_t code_n1 = live ? qs.code(min(lo + 1, qlast)) : 0u;
+    uint32_t code_n2 = live ? qs.code(min(lo + 2, qlast)) : 0u;
+    uint32_t code_n3 = live ? qs.code(min(lo + 3, qlast)) : 0u;
+    uint32_t prof_c = s_prof[live ? qs.code(lo) : 0u];
     uint32_t ring_c = live ? ring.at(lo) : 0u;
+    uint32_t ring_n1 = live ? ring.at(lo + 1) : 0u;
+    uint32_t ring_n2 = live ? ring.at(lo + 2) : 0u;
     int32_t blk = 0;     // steps taken in the current key block
     int32_t cbase = lo;  // lower strip's column at block step 0
     auto step = [&](int32_t s, int mode) {
       const int32_t c = lo + s;
       const bool lo_act = live && c <= hi;
       const bool hi_act = live && s >= 1 && c - 1 <= hi;
-      const uint32_t code_nn = lo_act ? clamp_code(__ldg(qp + min(c + 2, qlast))) : 0u;
-      const uint32_t prof_n = s_prof[code_n];
-      const uint32_t ring_n = lo_act ? ring.at(c + 1) : 0u;
+      const uint32_t code_n4 = lo_act ? qs.code(min(c + 4, qlast)) : 0u;
+      const uint32_t prof_n = s_prof[code_n1];
+      const uint32_t ring_n3 = lo_act ? ring.at(c + 3) : 0u;
       // (H, F) of the row above at column c: row -1 on the first strip, else the
       // previous strip's bottom row (dead where it never reached)
       uint32_t tHF;
@@ -386,21 +416,25 @@ __device__ __forceinline__ Outcome lane_pair_p16(const Pair& pr, bool valid, con
       uint32_t oH, oF;
       if (mode == 0) {
         if (has_n)
-          lane_step_p16<R, false, true>(Hl, HAl, El, K, sel, prof, prof_prev, nn2, D, Hup, Fup,
-                                        pos2, na2, nb2, mcm, 0, R - 1, 0, R - 1, 0u, oH, oF);
+          lane_step_p16<R, false, true, false>(Hl, HAl, El, K, sel, prof, prof_prev, nn2, D, Hup,
+                                               Fup, pos2, na2, nb2, mcm, 0u, 0u, oH, oF);
         else
-          lane_step_p16<R, false, false>(Hl, HAl, El, K, sel, prof, prof_prev, nn2, D, Hup, Fup,
-                                         pos2, na2, nb2, mcm, 0, R - 1, 0, R - 1, 0u, oH, oF);
+          lane_step_p16<R, false, false, false>(Hl, HAl, El, K, sel, prof, prof_prev, nn2, D, Hup,
+                                                Fup, pos2, na2, nb2, mcm, 0u, 0u, oH, oF);
       } else {
         const int32_t d0 = c - i0;
-        const int32_t lrlo = lo_act ? d0 - w : R;
-        const int32_t lrhi = lo_act ? min(d0 + w, tlen - 1 - i0) : -1;
         const int32_t dh = d0 - 1 - R;  // upper strip: column c-1 minus its first row
-        const int32_t hrlo = hi_act ? dh - w : R;
-        const int32_t hrhi = hi_act ? min(dh + w, tlen - 1 - i0 - R) : -1;
-        const uint32_t keep = (lo_act ? 0u : 0x0000FFFFu) | (hi_act ? 0u : 0xFFFF0000u);
-        lane_step_p16<R, true, true>(Hl, HAl, El, K, sel, prof, prof_prev, nn2, D, Hup, Fup, pos2,
-                                     na2, nb2, mcm, lrlo, lrhi, hrlo, hrhi, keep, oH, oF);
+        const uint32_t inband =
+            (lo_act ? bit_range(d0 - w, min(d0 + w, tlen - 1 - i0), R) : 0u) |
+            ((hi_act ? bit_range(dh - w, min(dh + w, tlen - 1 - i0 - R), R) : 0u) << 16);
+        if (mode == 2) {
+          const uint32_t keep = (lo_act ? 0u : 0x0000FFFFu) | (hi_act ? 0u : 0xFFFF0000u);
+          lane_step_p16<R, true, true, true>(Hl, HAl, El, K, sel, prof, prof_prev, nn2, D, Hup,
+                                             Fup, pos2, na2, nb2, mcm, inband, keep, oH, oF);
+        } else {
+          lane_step_p16<R, true, true, false>(Hl, HAl, El, K, sel, prof, prof_prev, nn2, D, Hup,
+                                              Fup, pos2, na2, nb2, mcm, inband, 0u, oH, oF);
+        }
       }
       if (hi_act) ring.at(c - 1) = prmt(oH, oF, 0x7632u);
       oH2 = oH1;
@@ -409,20 +443,29 @@ __device__ __forceinline__ Outcome lane_pair_p16(const Pair& pr, bool valid, con
       tHF_prev = tHF;
       prof_prev = prof;
       prof_c = prof_n;
-      code_n = code_nn;
-      ring_c = ring_n;
+      code_n1 = code_n2;
+      code_n2 = code_n3;
+      code_n3 = code_n4;
+      ring_c = ring_n1;
+      ring_n1 = ring_n2;
+      ring_n2 = ring_n3;
       if (++blk == kTagSteps) {
         fold_keys<R>(K, Blo, Bhi, cbase);
         cbase += kTagSteps;
         blk = 0;
       }
     };
+    // the first step (upper strip not started) and the steps past any lane's
+    // end (lower strip finished) keep state; the fast range never holds them
+    const int32_t nmin = __reduce_min_sync(0xffffffffu, live ? nsteps : kFar);
     int32_t s = 0;
+    step(s++, 2);
     if (fs <= fe) {
       for (; s < fs; ++s) step(s, 1);
       for (; s <= fe; ++s) step(s, 0);
     }
-    for (; s < nmax; ++s) step(s, 1);
+    for (; s < nmin - 1 && s < nmax; ++s) step(s, 1);
+    for (; s < nmax; ++s) step(s, 2);
     fold_keys<R>(K, Blo, Bhi, cbase);
     hi_prev = hi;
     if (live) {
@@ -436,7 +479,8 @@ __device__ __forceinline__ Outcome lane_pair_p16(const Pair& pr, bool valid, con
           if (i < tlen && !st.stop) {
             const int32_t bk = half ? Bhi[r] : Blo[r];
             const int32_t m = bk < 0 ? 0 : (bk >> 16);
-            const int32_t mj = bk < 0 ? -1 : (bk & 0xFFFF);
+            // a dead row's column is its last in-band column (-1: none)
+            const int32_t mj = m > 0 ? (bk & 0xFFFF) : (i - w <= qlen - 1 ? min(qlen - 1, i + w) : -1);
             // after the sweep, Hl holds H(i, hi) of both strips (each strip kept
             // its state once it had passed column hi)
             const bool g_in = reach && (qlen - 1 - i <= w) && (i - (qlen - 1) <= w);
