@@ -39,10 +39,13 @@ METRIC = "seed-extension GCUPS & extensions/s (bit-exact), batched vs plain; p50
 # Integer-ALU issue peak: 152 SMs x 128 int32 lanes per SM per clock (measured
 # issue-bound rate of IADD/IMNMX/PRMT/DPX ops on this GPU) x 2070 MHz max SM clock.
 SMS, LANES, MAX_MHZ = 152, 128, 2070.0
-# Algorithmic int32 instructions per cell with the fused DPX forms native on
-# sm_103a: S (byte permute), anchored diagonal (add + select), E and F
-# (add-max each), H (3-way max with 0), H - alpha, row max+column (add, max).
+# Algorithmic instructions per cell with the fused DPX forms native on sm_103a:
+# S (byte permute), anchored diagonal (multiply + add-min), E and F (add-max
+# with relu each), H (3-way max), H - alpha, row key (multiply-add + max): 9-10
+# in 32-bit; the packed 16-bit form does two cells per instruction.
 OPS_PER_CELL_INT32 = 10
+OPS_PER_CELL_PACKED = 5
+LANE_MAX_QLEN = 510  # one-lane (packed-capable) buckets: qlen + 2 <= 2^9
 WORKLOAD_TEXT = {
     "c1_tiny": "1,000 pairs, 100 bp queries, 116 bp targets, 2% sub / 0.2% indel",
     "c2_short": "1,000,000 pairs, qlen U[1,150], tlen = qlen + 200, 1% sub / 0.1% indel, 5% unrelated",
@@ -142,6 +145,22 @@ def reduce(world, value, op):
     t = torch.tensor([float(value)], dtype=torch.float64, device="cuda")
     dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def algorithmic_ops(b, cells, sc):
+    """Instructions the extension DP needs for this batch: cells of pairs that
+    the packed 16-bit class takes (score bound B = h0 + match*min(qlen,tlen)
+    with (B+1)*2^k and B*64+63 within int16, query within the one-lane
+    buckets) at OPS_PER_CELL_PACKED, the rest at OPS_PER_CELL_INT32."""
+    m = sc.match
+    k = 0
+    while (1 << k) < m + 1:
+        k += 1
+    bound = b.h0.astype(np.int64) + m * np.minimum(b.q_len, b.t_len).astype(np.int64)
+    packed = ((bound + 1) << k <= 32767) & (bound * 64 + 63 <= 32767) & (b.q_len <= LANE_MAX_QLEN)
+    c = cells.astype(np.float64)
+    ops = OPS_PER_CELL_PACKED * c[packed].sum() + OPS_PER_CELL_INT32 * c[~packed].sum()
+    return float(ops), float(c[packed].sum() / max(c.sum(), 1.0))
 
 
 def kernel_source_hash() -> str:
@@ -263,6 +282,7 @@ def run_xt(args):
         step()
     torch.cuda.synchronize()
     cells_step = int(cells.sum().item())
+    ops_step, packed_frac = algorithmic_ops(b, cells.cpu().numpy(), wl.scoring)
     ctx.set_timing(True)
     ctx.stats()
     sampler = ClockSampler(local)
@@ -287,7 +307,7 @@ def run_xt(args):
     value = total_cells / (ms_max / 1e3) / 1e9
     dp_ms = st["dp_ms"] / max(1, st["timed_calls"])
     peak = SMS * LANES * MAX_MHZ * 1e6 / 1e12
-    achieved = cells_step * OPS_PER_CELL_INT32 / (dp_ms / 1e3) / 1e12
+    achieved = ops_step / (dp_ms / 1e3) / 1e12
     traffic = profiled_traffic(wl.name)
     res = {
         "metric": METRIC, "value": round(value, 3), "unit": "GCUPS", "n_gpus": world,
@@ -302,12 +322,14 @@ def run_xt(args):
         "ext_per_s": round(total_pairs / (ms_max / 1e3), 1),
         "gpu_launches": st["launches"],
         "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
-                     "unit": "Tops/s (int32-instruction equivalents)",
+                     "unit": "Tops/s (int-ALU instructions)",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "kernel": "k_queue (extension DP, all bucket launches of one step)",
+                     "kernel": "extension DP launches of one step (k_lane packed/32-bit, k_queue)",
                      "kernel_ms_per_step": round(dp_ms, 4),
-                     "ops_per_cell": OPS_PER_CELL_INT32,
-                     "peak_basis": "152 SMs x 128 lanes x 2070 MHz (max clock), derived"},
+                     "ops_per_cell": {"packed16x2": OPS_PER_CELL_PACKED,
+                                      "int32": OPS_PER_CELL_INT32},
+                     "packed_cell_fraction": round(packed_frac, 4),
+                     "peak_basis": "issue peak, derived: 152 SMs x 128 lanes x 2070 MHz (max clock)"},
         "clocks": clocks,
     }
     if not args.no_plain:
