@@ -23,7 +23,7 @@ RESULT_FIELDS = ("score", "qle", "tle", "gscore", "gtle", "max_off", "status")
 EXPORTED = ("xt_ctx_create", "xt_ctx_destroy", "xt_ctx_sync", "xt_extend_batch",
             "xt_extend_batch_plain", "xt_extend_batch_host", "xt_status_str",
             "xt_ctx_last_error", "xt_ctx_set_schedule", "xt_ctx_set_timing", "xt_ctx_stats",
-            "xt_extend_batch_static")
+            "xt_extend_batch_static", "xt_ctx_set_graphs")
 XT_STATIC_MAX_PAIRS = 1 << 20
 
 
@@ -82,6 +82,8 @@ def load_library(path: str | None = None):
     lib.xt_ctx_set_schedule.restype = ctypes.c_int
     lib.xt_extend_batch_static.argtypes = batch_args[1:]
     lib.xt_extend_batch_static.restype = ctypes.c_int
+    lib.xt_ctx_set_graphs.argtypes = [P, ctypes.c_int]
+    lib.xt_ctx_set_graphs.restype = ctypes.c_int
     lib.xt_ctx_set_timing.argtypes = [P, ctypes.c_int]
     lib.xt_ctx_set_timing.restype = ctypes.c_int
     lib.xt_ctx_stats.argtypes = [P, ctypes.POINTER(xt_stats)]
@@ -111,6 +113,10 @@ def xt_ctx_sync(ctx: int, stream: int = 0) -> int:
 
 def xt_ctx_set_schedule(ctx: int, P: int, R: int) -> int:
     return load_library().xt_ctx_set_schedule(ctypes.c_void_p(ctx), int(P), int(R))
+
+
+def xt_ctx_set_graphs(ctx: int, enable: bool) -> int:
+    return load_library().xt_ctx_set_graphs(ctypes.c_void_p(ctx), int(bool(enable)))
 
 
 def xt_ctx_set_timing(ctx: int, enable: bool) -> int:
@@ -223,6 +229,9 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def set_graphs(self, enable: bool = True):
+        self._check(xt_ctx_set_graphs(self.handle, enable), "xt_ctx_set_graphs")
 
     def set_timing(self, enable: bool = True):
         self._check(xt_ctx_set_timing(self.handle, enable), "xt_ctx_set_timing")

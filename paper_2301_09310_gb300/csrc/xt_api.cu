@@ -5,11 +5,32 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "xt.h"
 #include "xt_kernels.cuh"
 
 using namespace xt;
+
+namespace {
+// A captured call: same scoring, schedule, capacity class and workspace.
+struct GraphKey {
+  int plain;
+  xt_scoring sc;
+  int forced_P, forced_R;
+  int n_cap_log2;
+  void* work;
+  void* pool;
+  bool has_cells;
+  bool operator==(const GraphKey& o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
+};
+struct GraphEntry {
+  GraphKey key;
+  int seen = 0;                   // calls with this key (captured on the second)
+  cudaGraphExec_t exec = nullptr;
+};
+constexpr int kDescSlots = 64;   // pinned staging slots for the per-call descriptor
+}  // namespace
 
 struct xt_ctx {
   int device = 0;
@@ -32,6 +53,14 @@ struct xt_ctx {
   cudaEvent_t ev[kEvRing][2] = {};
   int ev_pending = 0;
   int calls = 0, launches = 0, dp_launches = 0;
+  // per-call batch descriptor: pinned host slots copied to a device slot
+  xt::Batch* desc_host = nullptr;
+  cudaEvent_t desc_ev[kDescSlots] = {};
+  int desc_next = 0;
+  // CUDA graphs of whole calls
+  bool graphs = true;
+  cudaStream_t cap_stream = nullptr;
+  std::vector<GraphEntry> graph_cache;
   int match = 1;                 // scoring of the call being planned
   int forced_P = 0;              // schedule override (0: per-bucket table)
   int forced_R = 0;
@@ -115,9 +144,16 @@ xt_status dev_alloc(xt_ctx* ctx, void** p, size_t* have, size_t want) {
   return XT_OK;
 }
 
-// Carve the per-call workspace for n pairs.
-xt_status get_work(xt_ctx* ctx, int32_t n, Work* w) {
+void drop_graphs(xt_ctx* ctx) {
+  for (auto& g : ctx->graph_cache)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  ctx->graph_cache.clear();
+}
+
+// Carve the per-call workspace for n pairs (and the device batch descriptor).
+xt_status get_work(xt_ctx* ctx, int32_t n, Work* w, Batch** desc) {
   size_t off = 0;
+  const size_t o_desc = off; off = align_up(off + sizeof(Batch));
   const size_t o_pclass = off; off = align_up(off + (size_t)n);
   const size_t o_order = off; off = align_up(off + 4 * (size_t)n);
   const size_t o_counts = off; off = align_up(off + 4 * (size_t)kNumBuckets);
@@ -125,9 +161,12 @@ xt_status get_work(xt_ctx* ctx, int32_t n, Work* w) {
   const size_t o_sb = off; off = align_up(off + 4 * (size_t)(kNumClasses * kNumJ));
   const size_t o_se = off; off = align_up(off + 4 * (size_t)(kNumClasses * kNumJ));
   const size_t o_heads = off; off = align_up(off + 4 * (size_t)kMaxLaunches);
+  void* old = ctx->work;
   xt_status s = dev_alloc(ctx, &ctx->work, &ctx->work_bytes, off);
   if (s != XT_OK) return s;
+  if (ctx->work != old) drop_graphs(ctx);
   char* base = (char*)ctx->work;
+  *desc = (Batch*)(base + o_desc);
   w->pclass = (uint8_t*)(base + o_pclass);
   w->order = (int32_t*)(base + o_order);
   w->counts = (int32_t*)(base + o_counts);
@@ -311,6 +350,40 @@ xt_status check_args(xt_ctx* ctx, const void* q_seq, int64_t q_bytes, const void
   return XT_OK;
 }
 
+// Enqueue one call's work: reset counters, classify, order, extension kernels.
+cudaError_t enqueue(xt_ctx* ctx, bool plain, const Plan& pl, int plain_rs, const Score& sc,
+                    int32_t match, const Work& w, const Batch* desc, int32_t n_cap,
+                    cudaStream_t stream, int* dp_out) {
+  cudaError_t e = cudaMemsetAsync(w.counts, 0, 4 * (size_t)kNumBuckets, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.heads, 0, 4 * (size_t)kMaxLaunches, stream);
+  if (e == cudaSuccess) e = launch_classify(desc, n_cap, sc, match, pl.jf, w, stream);
+  if (e == cudaSuccess) e = launch_order(desc, n_cap, w, stream);
+  const int slot = ctx->ev_pending;
+  const bool timed = ctx->timing && slot < xt_ctx::kEvRing;
+  if (e == cudaSuccess && timed) {
+    for (int k = 0; k < 2; ++k)
+      if (!ctx->ev[slot][k]) cudaEventCreate(&ctx->ev[slot][k]);
+    cudaEventRecord(ctx->ev[slot][0], stream);
+  }
+  int dp = 0;
+  if (e == cudaSuccess && plain) {
+    e = launch_plain(desc, n_cap, sc, w, plain_rs, stream);
+    ++dp;
+  }
+  for (int i = 0; e == cudaSuccess && i < pl.n_launch; ++i) {
+    const Launch& L = pl.launch[i];
+    e = L.lane ? launch_lane(desc, sc, w, L, i, ctx->pool, stream)
+               : launch_queue(desc, sc, w, L, i, ctx->pool, stream);
+    ++dp;
+  }
+  if (e == cudaSuccess && timed) {
+    cudaEventRecord(ctx->ev[slot][1], stream);
+    ctx->ev_pending = slot + 1;
+  }
+  *dp_out = dp;
+  return e;
+}
+
 xt_status run(xt_ctx* ctx, bool plain, const uint8_t* q_seq, int64_t q_bytes, const int64_t* q_off,
               const int32_t* q_len, const uint8_t* t_seq, int64_t t_bytes, const int64_t* t_off,
               const int32_t* t_len, const int32_t* h0, int32_t n, const xt_scoring* scr,
@@ -323,7 +396,8 @@ xt_status run(xt_ctx* ctx, bool plain, const uint8_t* q_seq, int64_t q_bytes, co
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
   const Score sc = make_score(scr);
   Work w;
-  s = get_work(ctx, n, &w);
+  Batch* desc = nullptr;
+  s = get_work(ctx, n, &w, &desc);
   if (s != XT_OK) return s;
   Plan pl;
   int plain_rs = 0;
@@ -332,44 +406,74 @@ xt_status run(xt_ctx* ctx, bool plain, const uint8_t* q_seq, int64_t q_bytes, co
   else plan_batched(ctx, sc, &pl);
   const size_t want = pool_bytes(pl);
   if (want) {
+    void* old = ctx->pool;
     s = dev_alloc(ctx, (void**)&ctx->pool, &ctx->pool_bytes, want);
     if (s != XT_OK) return s;
+    if ((void*)ctx->pool != old) drop_graphs(ctx);
   }
-  Batch b;
-  b.q_seq = q_seq; b.t_seq = t_seq; b.q_off = q_off; b.t_off = t_off; b.q_len = q_len;
-  b.t_len = t_len; b.h0 = h0; b.q_bytes = q_bytes; b.t_bytes = t_bytes; b.n = n; b.out = out;
-  b.cells = cells;
-  // small control block: counts, heads and the bucket flags
-  e = cudaMemsetAsync(w.counts, 0, 4 * (size_t)kNumBuckets, stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(w.heads, 0, 4 * (size_t)kMaxLaunches, stream);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "workspace init");
-  e = launch_classify(b, sc, scr->match, pl.jf, w, stream);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "classify");
-  e = launch_order(b, w, stream);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "order");
-  const int slot = ctx->ev_pending;
-  const bool timed = ctx->timing && slot < xt_ctx::kEvRing;
-  if (timed) {
-    for (int k = 0; k < 2; ++k)
-      if (!ctx->ev[slot][k]) cudaEventCreate(&ctx->ev[slot][k]);
-    cudaEventRecord(ctx->ev[slot][0], stream);
-  }
+  // this call's arguments go to the device descriptor through a pinned slot
+  Batch hb;
+  hb.q_seq = q_seq; hb.t_seq = t_seq; hb.q_off = q_off; hb.t_off = t_off; hb.q_len = q_len;
+  hb.t_len = t_len; hb.h0 = h0; hb.q_bytes = q_bytes; hb.t_bytes = t_bytes; hb.n = n;
+  hb.out = out; hb.cells = cells;
+  const int slot = ctx->desc_next;
+  ctx->desc_next = (slot + 1) % kDescSlots;
+  e = cudaEventSynchronize(ctx->desc_ev[slot]);  // that slot's previous copy has run
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "descriptor slot");
+  ctx->desc_host[slot] = hb;
+  e = cudaMemcpyAsync(desc, &ctx->desc_host[slot], sizeof(Batch), cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->desc_ev[slot], stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "descriptor copy");
+  int n_cap_log2 = 10;
+  while ((1 << n_cap_log2) < n) ++n_cap_log2;
+  const int32_t n_cap = n_cap_log2 >= 31 ? INT32_MAX : (1 << n_cap_log2);
   int dp = 0;
-  if (plain) {
-    e = launch_plain(b, sc, w, plain_rs, stream);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "plain kernel");
-    ++dp;
+  GraphEntry* ge = nullptr;
+  if (ctx->graphs && !ctx->timing) {
+    GraphKey key;
+    std::memset(&key, 0, sizeof(key));
+    key.plain = plain; key.sc = *scr; key.forced_P = ctx->forced_P; key.forced_R = ctx->forced_R;
+    key.n_cap_log2 = n_cap_log2; key.work = ctx->work; key.pool = ctx->pool;
+    key.has_cells = cells != nullptr;
+    for (auto& g : ctx->graph_cache)
+      if (g.key == key) ge = &g;
+    if (!ge) {
+      if (ctx->graph_cache.size() >= 32) drop_graphs(ctx);
+      ctx->graph_cache.push_back(GraphEntry());
+      ge = &ctx->graph_cache.back();
+      ge->key = key;
+    }
+    ge->seen += 1;
+    if (!ge->exec && ge->seen >= 2) {
+      // capture this call's launches once on a private stream; the graph reads
+      // every per-call argument from the device descriptor
+      cudaGraph_t g = nullptr;
+      e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        cudaError_t e2 = enqueue(ctx, plain, pl, plain_rs, sc, scr->match, w, desc, n_cap,
+                                 ctx->cap_stream, &dp);
+        e = cudaStreamEndCapture(ctx->cap_stream, &g);
+        if (e == cudaSuccess) e = e2;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&ge->exec, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        // capture is an optimisation: on failure this and later calls launch directly
+        cudaGetLastError();
+        if (ge->exec) cudaGraphExecDestroy(ge->exec);
+        ge->exec = nullptr;
+        ctx->graphs = false;
+        ctx->last_error = std::string("graph capture disabled: ") + cudaGetErrorString(e);
+      }
+    }
   }
-  for (int i = 0; i < pl.n_launch; ++i) {
-    const Launch& L = pl.launch[i];
-    e = L.lane ? launch_lane(b, sc, w, L, i, ctx->pool, stream)
-               : launch_queue(b, sc, w, L, i, ctx->pool, stream);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, L.lane ? "lane kernel" : "queue kernel");
-    ++dp;
-  }
-  if (timed) {
-    cudaEventRecord(ctx->ev[slot][1], stream);
-    ctx->ev_pending = slot + 1;
+  if (ge && ge->exec) {
+    e = cudaGraphLaunch(ge->exec, stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
+    dp = plain ? 1 + pl.n_launch : pl.n_launch;
+  } else {
+    e = enqueue(ctx, plain, pl, plain_rs, sc, scr->match, w, desc, n_cap, stream, &dp);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "launch");
   }
   ctx->calls += 1;
   ctx->launches += 3 + dp;  // classify, scan, scatter + DP kernels
@@ -395,6 +499,16 @@ xt_status xt_ctx_create(xt_ctx** out, int device, size_t mem_budget_bytes) {
   c->budget = mem_budget_bytes;
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
   c->smem_optin = max_smem_per_block_optin(device);
+  bool ok = cudaHostAlloc((void**)&c->desc_host, sizeof(Batch) * kDescSlots,
+                          cudaHostAllocDefault) == cudaSuccess;
+  for (int k = 0; ok && k < kDescSlots; ++k)
+    ok = cudaEventCreateWithFlags(&c->desc_ev[k], cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    xt_ctx_destroy(c);
+    return XT_ECUDA;
+  }
   *out = c;
   return XT_OK;
 }
@@ -409,6 +523,11 @@ xt_status xt_ctx_destroy(xt_ctx* ctx) {
   for (auto& pr : ctx->ev)
     for (auto& e : pr)
       if (e) cudaEventDestroy(e);
+  drop_graphs(ctx);
+  for (auto& e : ctx->desc_ev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->desc_host) cudaFreeHost(ctx->desc_host);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   delete ctx;
   return XT_OK;
 }
@@ -491,6 +610,13 @@ xt_status xt_extend_batch_host(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_byte
     e = cudaMemcpyAsync(cells_out, d + o_cells, 8 * n, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "device to host copy");
+  return XT_OK;
+}
+
+xt_status xt_ctx_set_graphs(xt_ctx* ctx, int enable) {
+  if (!ctx) return XT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->graphs = enable != 0;
   return XT_OK;
 }
 
@@ -588,8 +714,9 @@ cudaError_t static_scratch(int device, void** ptr) {
 
 // Carve the Work tables for n pairs out of the scratch array; false if they
 // do not fit.
-bool carve_static(void* base_ptr, int32_t n, Work* w) {
+bool carve_static(void* base_ptr, int32_t n, Work* w, Batch** desc) {
   size_t off = 0;
+  const size_t o_desc = off; off = align_up(off + sizeof(Batch));
   const size_t o_pclass = off; off = align_up(off + (size_t)n);
   const size_t o_order = off; off = align_up(off + 4 * (size_t)n);
   const size_t o_counts = off; off = align_up(off + 4 * (size_t)kNumBuckets);
@@ -606,6 +733,7 @@ bool carve_static(void* base_ptr, int32_t n, Work* w) {
   w->seg_begin = (int32_t*)(base + o_sb);
   w->seg_end = (int32_t*)(base + o_se);
   w->heads = (int32_t*)(base + o_heads);
+  *desc = (Batch*)(base + o_desc);
   return true;
 }
 
@@ -642,21 +770,27 @@ extern "C" xt_status xt_extend_batch_static(const uint8_t* q_seq, int64_t q_byte
   void* base = nullptr;
   if (static_scratch(device, &base) != cudaSuccess) return XT_ECUDA;
   Work w;
-  if (!carve_static(base, n_pairs, &w)) return XT_EINVAL;
+  Batch* desc = nullptr;
+  if (!carve_static(base, n_pairs, &w, &desc)) return XT_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   Batch b;
   b.q_seq = q_seq; b.t_seq = t_seq; b.q_off = q_off; b.t_off = t_off; b.q_len = q_len;
   b.t_len = t_len; b.h0 = h0; b.q_bytes = q_bytes; b.t_bytes = t_bytes; b.n = n_pairs; b.out = out;
   b.cells = cells_out;
+  // the descriptor goes to the device copy from this stack frame; a copy
+  // from pageable memory is staged before the call returns
+  cudaError_t e0 = cudaMemcpyAsync(desc, &b, sizeof(Batch), cudaMemcpyHostToDevice, st);
+  if (e0 != cudaSuccess) return XT_ECUDA;
   // counters and queue heads start at zero on every call; the bucket flags
   // are rewritten; everything else is written before it is read
   cudaError_t e = cudaMemsetAsync(w.counts, 0, 4 * (size_t)kNumBuckets, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(w.heads, 0, 4 * (size_t)kMaxLaunches, st);
-  if (e == cudaSuccess) e = launch_classify(b, sc, scr->match, pl.jf, w, st);
-  if (e == cudaSuccess) e = launch_order(b, w, st);
+  if (e == cudaSuccess) e = launch_classify(desc, n_pairs, sc, scr->match, pl.jf, w, st);
+  if (e == cudaSuccess) e = launch_order(desc, n_pairs, w, st);
   for (int i = 0; e == cudaSuccess && i < pl.n_launch; ++i) {
     const Launch& L = pl.launch[i];
-    e = L.lane ? launch_lane(b, sc, w, L, i, nullptr, st) : launch_queue(b, sc, w, L, i, nullptr, st);
+    e = L.lane ? launch_lane(desc, sc, w, L, i, nullptr, st)
+               : launch_queue(desc, sc, w, L, i, nullptr, st);
   }
   return e == cudaSuccess ? XT_OK : XT_ECUDA;
 }

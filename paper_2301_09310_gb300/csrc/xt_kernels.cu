@@ -33,7 +33,9 @@ __device__ __forceinline__ void bucket_of(int32_t ql, int* j_out, int* sub_out) 
 // Validates every pair, writes the results of invalid and degenerate pairs
 // directly, and assigns the others a class and a (bucket, sub-bucket) by
 // query length, counted for the ordering pass.
-__global__ void k_classify(Batch b, Score sc, int32_t match, int32_t mshift, JFlags jfl, Work w) {
+__global__ void k_classify(const Batch* __restrict__ bd, Score sc, int32_t match, int32_t mshift,
+                           JFlags jfl, Work w) {
+  const Batch b = *bd;
   const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= b.n) return;
   const int64_t qo = b.q_off[k], to = b.t_off[k];
@@ -132,7 +134,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(Work w) {
   }
 }
 
-__global__ void k_scatter(Batch b, Work w) {
+__global__ void k_scatter(const Batch* __restrict__ bd, Work w) {
+  const Batch b = *bd;
   const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= b.n) return;
   const int cls = w.pclass[k];
@@ -157,13 +160,25 @@ __device__ __forceinline__ Pair load_pair(const Batch& b, int32_t k) {
 // ------------------------------------------------------- persistent queue
 // Groups of P lanes pull pairs of class `cls`, buckets [j_lo, j_hi], from a
 // device-side queue (one atomicAdd per pair) until it is empty.
+// The score profile goes to shared memory with constant indices: indexing the
+// by-value Score argument with threadIdx.x would move it to local memory.
+__device__ __forceinline__ void copy_profile(const Score& sc, uint32_t* s_prof) {
+#pragma unroll
+  for (int c = 0; c < 5; ++c) s_prof[c] = sc.prof[c];
+}
+
 template <int P, int R, bool WIDE>
 __global__ void __launch_bounds__(kQueueThreads)
-    k_queue(Batch b, Score sc, Work w, int cls, int j_lo, int j_hi, int head_id, int rs_log2,
-            int2* gring, int64_t slab) {
+    k_queue(const Batch* __restrict__ bd, Score sc, Work w, int cls, int j_lo, int j_hi,
+            int head_id, int rs_log2, int2* gring, int64_t slab) {
+  // batch arguments stay in shared memory and are read where used
+  __shared__ Batch s_b;
+  if (threadIdx.x == 0) s_b = *bd;
+  __syncthreads();
+  const Batch& b = s_b;
   extern __shared__ int2 s_ring[];
   __shared__ uint32_t s_prof[8];
-  if (threadIdx.x < 5) s_prof[threadIdx.x] = sc.prof[threadIdx.x];
+  if (threadIdx.x == 0) copy_profile(sc, s_prof);
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int p = threadIdx.x % P;
@@ -203,12 +218,16 @@ __global__ void __launch_bounds__(kQueueThreads)
 // of nearly equal length.
 template <int R, bool PACKED, bool GRING, bool QSTAGE>
 __global__ void __launch_bounds__(kLaneThreads, 4)
-    k_lane(Batch b, Score sc, Work w, int cls, int j_lo, int j_hi, int head_id, int rs_log2,
-           void* gring, int mparam, int qs_log2) {
+    k_lane(const Batch* __restrict__ bd, Score sc, Work w, int cls, int j_lo, int j_hi,
+           int head_id, int rs_log2, void* gring, int mparam, int qs_log2) {
+  // batch arguments stay in shared memory and are read where used
+  __shared__ Batch s_b;
+  if (threadIdx.x == 0) s_b = *bd;
+  const Batch& b = s_b;
   using T = typename Ring<PACKED>::T;
   extern __shared__ __align__(16) unsigned char s_dyn[];
   __shared__ uint32_t s_prof[8];
-  if (threadIdx.x < 5) s_prof[threadIdx.x] = sc.prof[threadIdx.x];
+  if (threadIdx.x == 0) copy_profile(sc, s_prof);
   __syncthreads();
   const int lane = threadIdx.x & 31;
   // ring: column c of lane t at [(c & mask) * kLaneThreads + t], so the lanes
@@ -261,13 +280,16 @@ __global__ void __launch_bounds__(kLaneThreads, 4)
 // ------------------------------------------------------------------ plain
 // One pair per thread block of one warp (P = 32 lanes, R = 8 rows per lane),
 // 32-bit arithmetic, no bucketing: the comparison kernel.
-__global__ void __launch_bounds__(32) k_plain(Batch b, Score sc, Work w, int rs_log2) {
+__global__ void __launch_bounds__(32) k_plain(const Batch* __restrict__ bd, Score sc, Work w,
+                                              int rs_log2) {
   extern __shared__ int2 s_ring[];
   __shared__ uint32_t s_prof[8];
+  const Batch b = *bd;
   const int32_t k = blockIdx.x;
+  if (k >= b.n) return;
   const int cls = w.pclass[k];
   if (cls != CLS_NARROW && cls != CLS_WIDE) return;
-  if (threadIdx.x < 5) s_prof[threadIdx.x] = sc.prof[threadIdx.x];
+  if (threadIdx.x == 0) copy_profile(sc, s_prof);
   __syncwarp();
   const Pair pr = load_pair(b, k);
   const int rmask = (1 << rs_log2) - 1;
@@ -281,21 +303,21 @@ __global__ void __launch_bounds__(32) k_plain(Batch b, Score sc, Work w, int rs_
 }
 
 // ---------------------------------------------------------------- launchers
-cudaError_t launch_classify(const Batch& b, const Score& sc, int32_t match, const JFlags& jf,
-                            const Work& w, cudaStream_t stream) {
-  if (b.n == 0) return cudaSuccess;
+cudaError_t launch_classify(const Batch* bd, int32_t n_cap, const Score& sc, int32_t match,
+                            const JFlags& jf, const Work& w, cudaStream_t stream) {
+  if (n_cap == 0) return cudaSuccess;
   const int T = 256;
   int mshift = 0;
   while ((1 << mshift) < match + 1) ++mshift;
-  k_classify<<<(b.n + T - 1) / T, T, 0, stream>>>(b, sc, match, mshift, jf, w);
+  k_classify<<<(n_cap + T - 1) / T, T, 0, stream>>>(bd, sc, match, mshift, jf, w);
   return cudaGetLastError();
 }
 
-cudaError_t launch_order(const Batch& b, const Work& w, cudaStream_t stream) {
+cudaError_t launch_order(const Batch* bd, int32_t n_cap, const Work& w, cudaStream_t stream) {
   k_scan<<<1, kScanThreads, 0, stream>>>(w);
-  if (b.n > 0) {
+  if (n_cap > 0) {
     const int T = 256;
-    k_scatter<<<(b.n + T - 1) / T, T, 0, stream>>>(b, w);
+    k_scatter<<<(n_cap + T - 1) / T, T, 0, stream>>>(bd, w);
   }
   return cudaGetLastError();
 }
@@ -305,7 +327,7 @@ size_t queue_smem_bytes(int P, int rs_log2) {
 }
 
 template <int P, int R, bool WIDE>
-static cudaError_t launch_queue_t(const Batch& b, const Score& sc, const Work& w, const Launch& L,
+static cudaError_t launch_queue_t(const Batch* b, const Score& sc, const Work& w, const Launch& L,
                                   int head_id, int2* gring, cudaStream_t stream) {
   const size_t smem = L.global_ring ? 0 : queue_smem_bytes(P, L.rs_log2);
   auto kern = k_queue<P, R, WIDE>;
@@ -321,7 +343,7 @@ static cudaError_t launch_queue_t(const Batch& b, const Score& sc, const Work& w
 }
 
 template <bool WIDE>
-static cudaError_t launch_queue_w(const Batch& b, const Score& sc, const Work& w, const Launch& L,
+static cudaError_t launch_queue_w(const Batch* b, const Score& sc, const Work& w, const Launch& L,
                                   int head_id, int2* gring, cudaStream_t stream) {
 #define XT_Q(PP, RR) \
   if (L.P == PP && L.R == RR) return launch_queue_t<PP, RR, WIDE>(b, sc, w, L, head_id, gring, stream);
@@ -332,7 +354,7 @@ static cudaError_t launch_queue_w(const Batch& b, const Score& sc, const Work& w
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_queue(const Batch& b, const Score& sc, const Work& w, const Launch& L,
+cudaError_t launch_queue(const Batch* b, const Score& sc, const Work& w, const Launch& L,
                          int head_id, int2* gring, cudaStream_t stream) {
   if (L.cls == CLS_NARROW) return launch_queue_w<false>(b, sc, w, L, head_id, gring, stream);
   return launch_queue_w<true>(b, sc, w, L, head_id, gring, stream);
@@ -347,7 +369,7 @@ size_t lane_stage_bytes(int j_hi) {
 }
 
 template <int R, bool PACKED, bool GRING, bool QSTAGE>
-static cudaError_t launch_lane_t(const Batch& b, const Score& sc, const Work& w, const Launch& L,
+static cudaError_t launch_lane_t(const Batch* b, const Score& sc, const Work& w, const Launch& L,
                                  int head_id, void* gring, cudaStream_t stream) {
   const size_t smem = (GRING ? 0 : kLaneThreads * lane_ring_bytes(L.cls, L.rs_log2)) +
                       (QSTAGE ? lane_stage_bytes(L.j_hi) : 0);
@@ -362,7 +384,7 @@ static cudaError_t launch_lane_t(const Batch& b, const Score& sc, const Work& w,
   return cudaGetLastError();
 }
 
-cudaError_t launch_lane(const Batch& b, const Score& sc, const Work& w, const Launch& L,
+cudaError_t launch_lane(const Batch* b, const Score& sc, const Work& w, const Launch& L,
                         int head_id, void* gring, cudaStream_t stream) {
   const bool packed = L.cls == CLS_PACKED;
   const bool stage = packed && lane_stage_bytes(L.j_hi) > 0;
@@ -390,16 +412,16 @@ cudaError_t launch_lane(const Batch& b, const Score& sc, const Work& w, const La
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_plain(const Batch& b, const Score& sc, const Work& w, int rs_log2,
-                         cudaStream_t stream) {
-  if (b.n == 0) return cudaSuccess;
+cudaError_t launch_plain(const Batch* b, int32_t n_cap, const Score& sc, const Work& w,
+                         int rs_log2, cudaStream_t stream) {
+  if (n_cap == 0) return cudaSuccess;
   const size_t smem = ((size_t)1 << rs_log2) * sizeof(int2);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_plain, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_plain<<<b.n, 32, smem, stream>>>(b, sc, w, rs_log2);
+  k_plain<<<n_cap, 32, smem, stream>>>(b, sc, w, rs_log2);
   return cudaGetLastError();
 }
 

@@ -57,14 +57,16 @@ struct Launch {
 struct JFlags {
   uint8_t f[kNumJ];
 };
-cudaError_t launch_classify(const Batch& b, const Score& sc, int32_t match, const JFlags& jf,
-                            const Work& w, cudaStream_t stream);
-cudaError_t launch_order(const Batch& b, const Work& w, cudaStream_t stream);
-cudaError_t launch_queue(const Batch& b, const Score& sc, const Work& w, const Launch& L,
+// Kernels read the batch arguments from a device copy (bd) so that one
+// captured graph serves every call; n_cap sizes the per-pair grids (>= n).
+cudaError_t launch_classify(const Batch* bd, int32_t n_cap, const Score& sc, int32_t match,
+                            const JFlags& jf, const Work& w, cudaStream_t stream);
+cudaError_t launch_order(const Batch* bd, int32_t n_cap, const Work& w, cudaStream_t stream);
+cudaError_t launch_queue(const Batch* bd, const Score& sc, const Work& w, const Launch& L,
                          int head_id, int2* gring, cudaStream_t stream);
-cudaError_t launch_plain(const Batch& b, const Score& sc, const Work& w, int rs_log2,
-                         cudaStream_t stream);
-cudaError_t launch_lane(const Batch& b, const Score& sc, const Work& w, const Launch& L,
+cudaError_t launch_plain(const Batch* bd, int32_t n_cap, const Score& sc, const Work& w,
+                         int rs_log2, cudaStream_t stream);
+cudaError_t launch_lane(const Batch* bd, const Score& sc, const Work& w, const Launch& L,
                         int head_id, void* gring, cudaStream_t stream);
 // Shared memory a queue launch needs per CTA (bytes).
 size_t queue_smem_bytes(int P, int rs_log2);

@@ -155,3 +155,26 @@ def test_repeat_calls_reuse_workspace(ctx):
     b2 = synth.generate(wl, n=7000, first=50000)
     for b in (b2, b1, b2):
         assert_same(run_gpu(ctx, b, wl.scoring), run_oracle(b, wl.scoring), "repeat")
+
+
+def test_graph_replay_matches_direct(ctx):
+    # the second call of a (scoring, size class) is captured, later ones replay
+    # the graph; each call brings its own arrays through the device descriptor
+    import paper_2301_09310_gb300 as xt
+    wl = synth.WORKLOADS["c3_mixed"]
+    batches = [synth.generate(wl, n=n, first=f) for n, f in
+               ((3000, 0), (2900, 10000), (2048, 20000), (3000, 30000), (1500, 40000))]
+    want = []
+    direct = xt.Context(0)
+    direct.set_graphs(False)
+    try:
+        for b in batches:
+            want.append(run_gpu(direct, b, wl.scoring))
+    finally:
+        direct.close()
+    ctx.set_graphs(True)
+    for rep in range(2):
+        for b, w in zip(batches, want):
+            assert_same(run_gpu(ctx, b, wl.scoring), w, f"graph replay {rep}")
+    for b in batches[:2]:
+        assert_same(run_gpu(ctx, b, wl.scoring), run_oracle(b, wl.scoring), "graph vs oracle")
