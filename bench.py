@@ -68,6 +68,13 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-pairs", type=int, default=4_000_000,
+                    help="pairs of the c5 stream per offered-load level")
+    ap.add_argument("--streams", type=int, default=0,
+                    help="streams the extension kernels of a call fork onto (0: library default)")
+    ap.add_argument("--serve-slots", type=int, default=3)
+    ap.add_argument("--serve-gather-threads", type=int, default=0, help="0: library default")
     return ap.parse_args()
 
 
@@ -273,6 +280,8 @@ def run_xt(args):
     out = torch.empty((n, 7), dtype=torch.int32, device=dev)
     cells = torch.empty(n, dtype=torch.int64, device=dev)
     ctx = xt.Context(local)
+    if args.streams:
+        ctx.set_streams(args.streams)
     stream = torch.cuda.current_stream(dev)
 
     def step(plain=False):
@@ -356,6 +365,8 @@ def run_xt(args):
         res["speedup_vs_plain"] = round(pms / ms, 3)
     if not args.no_e2e:
         res["e2e"] = e2e_leg(ctx, b, wl, args, dev, stream, world)
+    if not args.no_serve and world == 1:
+        res["serving"] = serve_leg(args, local, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = oracle_sample(wl, args.cpu_seconds, first=0)
     ctx.close()
@@ -394,6 +405,141 @@ def e2e_leg(ctx, b, wl, args, dev, stream, world):
     return {"value": round(total_cells / dt / 1e9, 3), "unit": "GCUPS",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "ms_per_step": round(dt * 1e3, 3), "api": "xt_extend_batch_host (pinned host buffers)"}
+
+
+def serve_leg(args, local, stream):
+    """The c5 served stream through the serving loop (xt_serve_*): requests of
+    U[1,4096] host pairs arriving as a Poisson process at 25/50/90% of the
+    batched path's peak pairs/s on the same mix.  Latency of a request is from
+    its scheduled arrival to its results in host memory (xt_serve_times
+    stamps, CLOCK_MONOTONIC, the clock of time.monotonic_ns)."""
+    import ctypes
+    import queue
+    import threading
+
+    import torch
+    import paper_2301_09310_gb300 as xt
+    from paper_2301_09310_gb300 import synth
+
+    wl = synth.WORKLOADS["c5_stream"]
+    b = synth.generate(wl, n=args.serve_pairs)
+    dev = torch.device("cuda", local)
+    # peak of the batched path on this mix: device-resident, one call per step
+    ctx = xt.Context(local)
+    d = [torch.from_numpy(a).to(dev) for a in
+         (b.q_seq, b.q_off, b.q_len, b.t_seq, b.t_off, b.t_len, b.h0)]
+    out_d = torch.empty((b.n, 7), dtype=torch.int32, device=dev)
+    cells_d = torch.empty(b.n, dtype=torch.int64, device=dev)
+    for _ in range(3):
+        ctx.extend(*d, wl.scoring, out=out_d, cells=cells_d, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.extend(*d, wl.scoring, out=out_d, cells=cells_d, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    peak_ms = e0.elapsed_time(e1) / reps
+    peak_pairs = b.n / (peak_ms / 1e3)
+    ref_out, ref_cells = out_d.cpu().numpy(), cells_d.cpu().numpy()
+    total_cells = int(ref_cells.sum())
+    ctx.close()
+    del d, out_d, cells_d
+    lib = xt.load_library()
+    sc = xt._scoring(wl.scoring)
+    old_switch = sys.getswitchinterval()
+    sys.setswitchinterval(2e-4)
+    levels = []
+    for frac in (0.25, 0.5, 0.9):
+        rs = synth.request_stream(b, frac * peak_pairs, seed=5)
+        nreq = int(rs.size.size)
+        out = np.zeros((b.n, 7), np.int32)
+        cells = np.zeros(b.n, np.int64)
+        calls = []
+        for r in range(nreq):
+            q_seq, q_off, q_len, t_seq, t_off, t_len, h0 = rs.request(r)
+            a = int(rs.start[r])
+            calls.append((ctypes.c_void_p(q_seq.ctypes.data), q_seq.size,
+                          ctypes.c_void_p(q_off.ctypes.data), ctypes.c_void_p(q_len.ctypes.data),
+                          ctypes.c_void_p(t_seq.ctypes.data), t_seq.size,
+                          ctypes.c_void_p(t_off.ctypes.data), ctypes.c_void_p(t_len.ctypes.data),
+                          ctypes.c_void_p(h0.ctypes.data), int(rs.size[r]), ctypes.byref(sc),
+                          ctypes.c_void_p(out.ctypes.data + 28 * a),
+                          ctypes.c_void_p(cells.ctypes.data + 8 * a)))
+        srv = xt.xt_serve_create(local, xt.xt_serve_config(args.serve_slots, 0, 0, 0, 0,
+                                                           args.serve_gather_threads))
+        tickets = queue.Queue()
+        stamps = np.zeros((nreq, 4), np.int64)   # arrival, submit, launch, done
+        bpairs = np.zeros(nreq, np.int64)
+        status = []
+
+        def waiter():
+            for r in range(nreq):
+                tk = tickets.get()
+                s, tm = xt.xt_serve_wait(srv, tk, -1)
+                if s != xt.XT_OK:
+                    status.append(s)
+                stamps[r, 1:] = (tm.submit_ns, tm.launch_ns, tm.done_ns)
+                bpairs[r] = tm.batch_pairs
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        t0 = time.monotonic_ns() + 5_000_000
+        arrive = t0 + (rs.arrival_s * 1e9).astype(np.int64)
+        stamps[:, 0] = arrive
+        busy = 0
+        tk = ctypes.c_uint64(0)
+        submit = lib.xt_serve_submit
+        for r in range(nreq):
+            while True:
+                left = int(arrive[r]) - time.monotonic_ns()
+                if left <= 0:
+                    break
+                if left > 300_000:
+                    time.sleep((left - 200_000) / 1e9)
+            while True:
+                s = submit(ctypes.c_void_p(srv), *calls[r], ctypes.byref(tk))
+                if s != xt.XT_EBUSY:
+                    break
+                busy += 1
+            if s != xt.XT_OK:
+                raise RuntimeError(f"xt_serve_submit: {xt.xt_status_str(s)}")
+            tickets.put(tk.value)
+        th.join()
+        st = xt.xt_serve_get_stats(srv)
+        xt.xt_serve_destroy(srv)
+        if status:
+            raise RuntimeError(f"served requests failed: {set(status)}")
+        lat = (stamps[:, 3] - stamps[:, 0]) / 1e6
+        span = (stamps[:, 3].max() - t0) / 1e9
+        levels.append({
+            "offered_frac_of_peak": frac,
+            "offered_pairs_per_s": round(frac * peak_pairs, 1),
+            "achieved_pairs_per_s": round(b.n / span, 1),
+            "gcups": round(total_cells / span / 1e9, 3),
+            "p50_ms": round(float(np.percentile(lat, 50)), 3),
+            "p99_ms": round(float(np.percentile(lat, 99)), 3),
+            "queue_p99_ms": round(float(np.percentile((stamps[:, 2] - stamps[:, 1]) / 1e6, 99)), 3),
+            "submit_lag_p99_ms": round(float(np.percentile((stamps[:, 1] - stamps[:, 0]) / 1e6,
+                                                           99)), 3),
+            "mean_batch_pairs": round(float(np.mean(bpairs)), 1),
+            "batches": st.batches,
+            "gather_ms_per_batch": round(st.gather_ns / 1e6 / max(1, st.batches), 3),
+            "device_ms_per_batch": round(st.device_ns / 1e6 / max(1, st.batches), 3),
+            "requests": nreq, "busy_retries": busy,
+            "equal_to_batched": bool(np.array_equal(out, ref_out)
+                                     and np.array_equal(cells, ref_cells)),
+        })
+    sys.setswitchinterval(old_switch)
+    return {"workload": f"c5_stream: {args.serve_pairs:,} pairs, qlen lognormal median 120 "
+                        "sigma 1 clipped [1,2000], tlen = qlen + 200; requests U[1,4096] "
+                        "pairs, Poisson arrivals",
+            "api": f"xt_serve_submit/xt_serve_wait (host buffers; {args.serve_slots} slots, "
+                   f"gather threads {args.serve_gather_threads or 'default'})",
+            "latency": "scheduled arrival -> results in host memory",
+            "peak_batched_pairs_per_s": round(peak_pairs, 1),
+            "peak_batched_gcups": round(total_cells / (peak_ms / 1e3) / 1e9, 3),
+            "levels": levels}
 
 
 def _max_op():

@@ -193,6 +193,20 @@ xt_status xt_ctx_set_timing(xt_ctx* ctx, int enable);
 xt_status xt_ctx_set_graphs(xt_ctx* ctx, int enable);
 xt_status xt_ctx_stats(xt_ctx* ctx, xt_stats* out);
 
+/*
+ * Concurrency of the extension kernels of one call.  The batched path's
+ * per-bucket kernels are independent; they fork onto up to `branches`
+ * internal streams (forked from and joined back into the call's stream, so
+ * the call stays ordered on it) and run concurrently.  Kernels that share the
+ * global ring pool stay in order on one branch.  1..8 (default 8); 1 runs
+ * every kernel on the call's stream.  Results never depend on it.
+ */
+#define XT_MAX_BRANCHES 8
+xt_status xt_ctx_set_streams(xt_ctx* ctx, int branches);
+
+/* XT_OK if the scoring record is within the ranges above, else XT_EINVAL. */
+xt_status xt_scoring_check(const xt_scoring* sc);
+
 /* Human-readable name of a status code (static storage). */
 const char* xt_status_str(xt_status s);
 
@@ -232,6 +246,108 @@ xt_status xt_extend_batch_static(const uint8_t* q_seq, int64_t q_bytes, const in
                                  const int64_t* t_off, const int32_t* t_len, const int32_t* h0,
                                  int32_t n_pairs, const xt_scoring* sc, xt_result* out,
                                  int64_t* cells_out, void* stream);
+
+/*
+ * Serving loop: requests of host pairs, continuous batching on the GPU.
+ *
+ * Not part of the paper's method (which extends one batch per call): this is
+ * the runtime that feeds a stream of small requests into the batched path.
+ * A server owns one thread, `slots` contexts with a stream each, and per slot
+ * a pinned host staging buffer and a device buffer of max_batch_bytes.
+ * Whenever a slot is free and requests are waiting, the thread forms a batch
+ * from the waiting requests in arrival order (requests with the same scoring
+ * record as the oldest one, until the slot's pair or byte capacity is
+ * reached), gathers their pairs into the staging buffer (offsets rebased; a
+ * pair whose sequence lies outside its request's buffer gets status
+ * XT_EINVAL), copies it to the device with one copy, runs xt_extend_batch,
+ * and copies the results back with one copy.  While one slot's batch runs,
+ * the next forms and copies on another.  When a batch completes, the thread
+ * writes each request's results to the caller's output arrays and marks the
+ * request done.  Results are identical to one xt_extend_batch call on the
+ * request alone (pairs are independent).
+ *
+ * Admission: a request larger than one slot (pairs or staged bytes) is
+ * rejected with XT_EINVAL; while the bytes of waiting requests would exceed
+ * max_queued_bytes, xt_serve_submit returns XT_EBUSY and the caller retries.
+ * Device memory: slots x (staging + result buffers + context workspace);
+ * mem_budget_bytes caps the total (XT_ENOMEM at create or in a batch).
+ */
+typedef struct xt_server xt_server;
+
+typedef struct {
+  int32_t slots;            /* batches in flight at once, 1..8 (0: 3) */
+  int32_t max_batch_pairs;  /* pairs per batch, <= 1 << 24 (0: 1 << 20) */
+  int64_t max_batch_bytes;  /* staged input bytes per batch: sequences plus
+                               28 bytes per pair (0: 128 MiB) */
+  int64_t max_queued_bytes; /* staged bytes of waiting requests (0: 1 GiB) */
+  size_t mem_budget_bytes;  /* device memory of the whole server (0: no cap) */
+  int32_t gather_threads;   /* host threads staging a batch, 1..16, the server
+                               thread included (0: a quarter of the cores, <= 8) */
+} xt_serve_config;
+
+/* Latency stamps of one request, ns on CLOCK_MONOTONIC (see xt_now_ns). */
+typedef struct {
+  int64_t submit_ns;   /* xt_serve_submit accepted it */
+  int64_t launch_ns;   /* its batch was formed (left the waiting queue) */
+  int64_t done_ns;     /* its results were in the caller's output arrays */
+  int32_t batch_pairs; /* pairs of the batch that carried it */
+  int32_t status;      /* XT_OK, or the error of its batch (XT_ECUDA, XT_ENOMEM) */
+} xt_serve_times;
+
+typedef struct {
+  int64_t requests;    /* completed requests */
+  int64_t pairs;       /* their pairs */
+  int64_t cells;       /* their useful cells */
+  int64_t batches;     /* batches run */
+  int64_t waiting;     /* requests waiting for a batch now */
+  int64_t in_flight;   /* batches on the GPU now */
+  int64_t gather_ns;   /* host time spent staging batches (summed) */
+  int64_t device_ns;   /* stream time from copy-in start to copy-out end (summed) */
+} xt_serve_stats;
+
+/* Monotonic clock of the latency stamps (CLOCK_MONOTONIC, ns). */
+int64_t xt_now_ns(void);
+
+/* Start a server on `device`; cfg may be NULL (all defaults). */
+xt_status xt_serve_create(xt_server** server, int device, const xt_serve_config* cfg);
+
+/*
+ * Queue one request of n_pairs >= 0 host pairs (same layout and meaning as
+ * xt_extend_batch, every pointer a HOST pointer).  The caller keeps every
+ * array alive and unchanged, and the output arrays (out: xt_result[n_pairs];
+ * cells_out: int64[n_pairs] or NULL) untouched, until the request is done.
+ * *ticket identifies it.  Errors, all synchronous: XT_EINVAL (arguments,
+ * scoring, a request larger than one slot), XT_EBUSY (queue full, retry).
+ */
+xt_status xt_serve_submit(xt_server* server, const uint8_t* q_seq, int64_t q_bytes,
+                          const int64_t* q_off, const int32_t* q_len, const uint8_t* t_seq,
+                          int64_t t_bytes, const int64_t* t_off, const int32_t* t_len,
+                          const int32_t* h0, int32_t n_pairs, const xt_scoring* sc,
+                          xt_result* out, int64_t* cells_out, uint64_t* ticket);
+
+/* *done = 1 when the request's results are in its output arrays. */
+xt_status xt_serve_poll(xt_server* server, uint64_t ticket, int* done);
+
+/*
+ * Wait up to timeout_us microseconds (< 0: no limit) for a request.  On
+ * completion the ticket is released, `times` (may be NULL) receives its
+ * stamps, and the request's status is returned.  XT_ETIMEOUT if it is not
+ * done in time (the ticket stays valid); XT_EINVAL for an unknown ticket.
+ */
+xt_status xt_serve_wait(xt_server* server, uint64_t ticket, int64_t timeout_us,
+                        xt_serve_times* times);
+
+/*
+ * paused != 0: form no new batches (batches in flight finish; requests keep
+ * queueing up to max_queued_bytes).  paused = 0 resumes.  xt_serve_destroy
+ * resumes a paused server to finish its queue.
+ */
+xt_status xt_serve_pause(xt_server* server, int paused);
+
+xt_status xt_serve_get_stats(xt_server* server, xt_serve_stats* out);
+
+/* Finish every queued request, stop the thread and free the server. */
+xt_status xt_serve_destroy(xt_server* server);
 
 #ifdef __cplusplus
 }

@@ -23,7 +23,9 @@ RESULT_FIELDS = ("score", "qle", "tle", "gscore", "gtle", "max_off", "status")
 EXPORTED = ("xt_ctx_create", "xt_ctx_destroy", "xt_ctx_sync", "xt_extend_batch",
             "xt_extend_batch_plain", "xt_extend_batch_host", "xt_status_str",
             "xt_ctx_last_error", "xt_ctx_set_schedule", "xt_ctx_set_timing", "xt_ctx_stats",
-            "xt_extend_batch_static", "xt_ctx_set_graphs")
+            "xt_extend_batch_static", "xt_ctx_set_graphs", "xt_scoring_check", "xt_now_ns",
+            "xt_serve_create", "xt_serve_submit", "xt_serve_poll", "xt_serve_wait",
+            "xt_serve_pause", "xt_serve_get_stats", "xt_serve_destroy", "xt_ctx_set_streams")
 XT_STATIC_MAX_PAIRS = 1 << 20
 
 
@@ -36,6 +38,24 @@ class xt_stats(ctypes.Structure):
     _fields_ = [("calls", ctypes.c_int32), ("launches", ctypes.c_int32),
                 ("dp_launches", ctypes.c_int32), ("timed_calls", ctypes.c_int32),
                 ("dp_ms", ctypes.c_double)]
+
+
+class xt_serve_config(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("max_batch_pairs", ctypes.c_int32),
+                ("max_batch_bytes", ctypes.c_int64), ("max_queued_bytes", ctypes.c_int64),
+                ("mem_budget_bytes", ctypes.c_size_t), ("gather_threads", ctypes.c_int32)]
+
+
+class xt_serve_times(ctypes.Structure):
+    _fields_ = [("submit_ns", ctypes.c_int64), ("launch_ns", ctypes.c_int64),
+                ("done_ns", ctypes.c_int64), ("batch_pairs", ctypes.c_int32),
+                ("status", ctypes.c_int32)]
+
+
+class xt_serve_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in
+                ("requests", "pairs", "cells", "batches", "waiting", "in_flight",
+                 "gather_ns", "device_ns")]
 
 
 class XtError(RuntimeError):
@@ -84,12 +104,29 @@ def load_library(path: str | None = None):
     lib.xt_extend_batch_static.restype = ctypes.c_int
     lib.xt_ctx_set_graphs.argtypes = [P, ctypes.c_int]
     lib.xt_ctx_set_graphs.restype = ctypes.c_int
+    lib.xt_ctx_set_streams.argtypes = [P, ctypes.c_int]
+    lib.xt_ctx_set_streams.restype = ctypes.c_int
     lib.xt_ctx_set_timing.argtypes = [P, ctypes.c_int]
     lib.xt_ctx_set_timing.restype = ctypes.c_int
     lib.xt_ctx_stats.argtypes = [P, ctypes.POINTER(xt_stats)]
     lib.xt_ctx_stats.restype = ctypes.c_int
     lib.xt_ctx_last_error.argtypes = [P]
     lib.xt_ctx_last_error.restype = ctypes.c_char_p
+    lib.xt_scoring_check.argtypes = [ctypes.POINTER(xt_scoring)]
+    lib.xt_scoring_check.restype = ctypes.c_int
+    lib.xt_now_ns.argtypes = []
+    lib.xt_now_ns.restype = ctypes.c_int64
+    lib.xt_serve_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(xt_serve_config)]
+    lib.xt_serve_submit.argtypes = [P] + batch_args[1:-1] + [ctypes.POINTER(ctypes.c_uint64)]
+    lib.xt_serve_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]
+    lib.xt_serve_wait.argtypes = [P, ctypes.c_uint64, ctypes.c_int64,
+                                  ctypes.POINTER(xt_serve_times)]
+    lib.xt_serve_pause.argtypes = [P, ctypes.c_int]
+    lib.xt_serve_get_stats.argtypes = [P, ctypes.POINTER(xt_serve_stats)]
+    lib.xt_serve_destroy.argtypes = [P]
+    for fn in ("xt_serve_create", "xt_serve_submit", "xt_serve_poll", "xt_serve_wait",
+               "xt_serve_pause", "xt_serve_get_stats", "xt_serve_destroy", "xt_ctx_set_streams"):
+        getattr(lib, fn).restype = ctypes.c_int
     _LIB = lib
     return lib
 
@@ -119,6 +156,10 @@ def xt_ctx_set_graphs(ctx: int, enable: bool) -> int:
     return load_library().xt_ctx_set_graphs(ctypes.c_void_p(ctx), int(bool(enable)))
 
 
+def xt_ctx_set_streams(ctx: int, branches: int) -> int:
+    return load_library().xt_ctx_set_streams(ctypes.c_void_p(ctx), int(branches))
+
+
 def xt_ctx_set_timing(ctx: int, enable: bool) -> int:
     return load_library().xt_ctx_set_timing(ctypes.c_void_p(ctx), int(bool(enable)))
 
@@ -129,6 +170,65 @@ def xt_ctx_stats(ctx: int) -> xt_stats:
     if s != XT_OK:
         raise XtError(s, "xt_ctx_stats")
     return st
+
+
+def xt_scoring_check(sc) -> int:
+    return load_library().xt_scoring_check(ctypes.byref(_scoring(sc)))
+
+
+def xt_now_ns() -> int:
+    """The serving loop's clock (CLOCK_MONOTONIC, ns)."""
+    return load_library().xt_now_ns()
+
+
+def xt_serve_create(device: int = 0, cfg: xt_serve_config | None = None) -> int:
+    h = ctypes.c_void_p()
+    s = load_library().xt_serve_create(ctypes.byref(h), int(device),
+                                       ctypes.byref(cfg) if cfg is not None else None)
+    if s != XT_OK:
+        raise XtError(s, "xt_serve_create")
+    return h.value
+
+
+def xt_serve_submit(server, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off, t_len, h0, n, sc,
+                    out, cells) -> tuple[int, int]:
+    """Raw host pointers (ints) as in include/xt.h; returns (xt_status, ticket)."""
+    ticket = ctypes.c_uint64(0)
+    s = load_library().xt_serve_submit(
+        ctypes.c_void_p(server), ctypes.c_void_p(q_seq), int(q_bytes), ctypes.c_void_p(q_off),
+        ctypes.c_void_p(q_len), ctypes.c_void_p(t_seq), int(t_bytes), ctypes.c_void_p(t_off),
+        ctypes.c_void_p(t_len), ctypes.c_void_p(h0), int(n), ctypes.byref(_scoring(sc)),
+        ctypes.c_void_p(out), ctypes.c_void_p(cells), ctypes.byref(ticket))
+    return s, ticket.value
+
+
+def xt_serve_poll(server, ticket: int) -> tuple[int, bool]:
+    done = ctypes.c_int(0)
+    s = load_library().xt_serve_poll(ctypes.c_void_p(server), ticket, ctypes.byref(done))
+    return s, bool(done.value)
+
+
+def xt_serve_wait(server, ticket: int, timeout_us: int = -1) -> tuple[int, xt_serve_times]:
+    t = xt_serve_times()
+    s = load_library().xt_serve_wait(ctypes.c_void_p(server), ticket, int(timeout_us),
+                                     ctypes.byref(t))
+    return s, t
+
+
+def xt_serve_pause(server, paused: bool) -> int:
+    return load_library().xt_serve_pause(ctypes.c_void_p(server), int(bool(paused)))
+
+
+def xt_serve_get_stats(server) -> xt_serve_stats:
+    st = xt_serve_stats()
+    s = load_library().xt_serve_get_stats(ctypes.c_void_p(server), ctypes.byref(st))
+    if s != XT_OK:
+        raise XtError(s, "xt_serve_get_stats")
+    return st
+
+
+def xt_serve_destroy(server) -> int:
+    return load_library().xt_serve_destroy(ctypes.c_void_p(server))
 
 
 def xt_status_str(s: int) -> str:
@@ -233,6 +333,9 @@ class Context:
     def set_graphs(self, enable: bool = True):
         self._check(xt_ctx_set_graphs(self.handle, enable), "xt_ctx_set_graphs")
 
+    def set_streams(self, branches: int):
+        self._check(xt_ctx_set_streams(self.handle, branches), "xt_ctx_set_streams")
+
     def set_timing(self, enable: bool = True):
         self._check(xt_ctx_set_timing(self.handle, enable), "xt_ctx_set_timing")
 
@@ -310,3 +413,79 @@ class Context:
                   p(cells), stream.cuda_stream)
         self._check(s, "xt_extend_batch_host")
         return out, cells
+
+
+class Server:
+    """The serving loop (xt_serve_*) on numpy host arrays.
+
+    submit() queues one request and returns its ticket; the arrays passed
+    (and the result arrays it allocates) are kept alive here until wait()
+    releases the ticket.  wait() returns (out [n, 7] int32, cells [n] int64,
+    times dict) or raises XtError with the request's status."""
+
+    def __init__(self, device: int = 0, slots: int = 0, max_batch_pairs: int = 0,
+                 max_batch_bytes: int = 0, max_queued_bytes: int = 0, mem_budget_bytes: int = 0,
+                 gather_threads: int = 0):
+        cfg = xt_serve_config(slots, max_batch_pairs, max_batch_bytes, max_queued_bytes,
+                              mem_budget_bytes, gather_threads)
+        self.handle = xt_serve_create(device, cfg)
+        self._live = {}
+
+    def submit(self, q_seq, q_off, q_len, t_seq, t_off, t_len, h0, scoring, want_cells=True,
+               retry_busy: bool = False) -> int:
+        import numpy as np
+        arrs = [np.ascontiguousarray(a, dt) for a, dt in
+                ((q_seq, np.uint8), (q_off, np.int64), (q_len, np.int32), (t_seq, np.uint8),
+                 (t_off, np.int64), (t_len, np.int32), (h0, np.int32))]
+        n = int(arrs[2].size)
+        out = np.empty((n, 7), np.int32)
+        cells = np.empty(n, np.int64) if want_cells else None
+        p = lambda a: a.ctypes.data if a is not None and a.size else 0  # noqa: E731
+        while True:
+            s, ticket = xt_serve_submit(self.handle, p(arrs[0]), arrs[0].size, p(arrs[1]),
+                                        p(arrs[2]), p(arrs[3]), arrs[3].size, p(arrs[4]),
+                                        p(arrs[5]), p(arrs[6]), n, scoring, p(out), p(cells))
+            if s == XT_EBUSY and retry_busy:
+                continue
+            if s != XT_OK:
+                raise XtError(s, "xt_serve_submit")
+            self._live[ticket] = (arrs, out, cells)
+            return ticket
+
+    def poll(self, ticket: int) -> bool:
+        s, done = xt_serve_poll(self.handle, ticket)
+        if s != XT_OK:
+            raise XtError(s, "xt_serve_poll")
+        return done
+
+    def wait(self, ticket: int, timeout_s: float | None = None):
+        us = -1 if timeout_s is None else int(timeout_s * 1e6)
+        s, t = xt_serve_wait(self.handle, ticket, us)
+        if s == XT_ETIMEOUT:
+            raise XtError(s, "xt_serve_wait")
+        _, out, cells = self._live.pop(ticket, (None, None, None))
+        if s != XT_OK:
+            raise XtError(s, "xt_serve_wait")
+        times = {f: getattr(t, f) for f, _ in xt_serve_times._fields_}
+        return out, cells, times
+
+    def pause(self, paused: bool = True):
+        s = xt_serve_pause(self.handle, paused)
+        if s != XT_OK:
+            raise XtError(s, "xt_serve_pause")
+
+    def stats(self) -> dict:
+        st = xt_serve_get_stats(self.handle)
+        return {f: getattr(st, f) for f, _ in xt_serve_stats._fields_}
+
+    def close(self):
+        if self.handle:
+            xt_serve_destroy(self.handle)
+            self.handle = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

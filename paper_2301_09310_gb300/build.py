@@ -20,7 +20,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
-CU_SOURCES = ["xt_api.cu", "xt_kernels.cu"]
+CU_SOURCES = ["xt_api.cu", "xt_kernels.cu", "xt_serve.cpp"]
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -60,7 +60,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     objs = []
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", f".{tag}.o"))
+        obj = os.path.join(BUILD, os.path.splitext(os.path.basename(src))[0] + f".{tag}.o")
         cmd = [nvcc(), "-c", os.path.join(CSRC, src), "-o", obj] + common
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0 or verbose:
@@ -72,7 +72,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     with ThreadPoolExecutor(max_workers=len(CU_SOURCES)) as ex:
         objs = list(ex.map(compile_one, CU_SOURCES))
     tmp = out + f".tmp{os.getpid()}"
-    cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH_FLAGS + ["-Xcompiler", "-fPIC"]
+    cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH_FLAGS + ["-Xcompiler", "-fPIC,-pthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         sys.stderr.write(r.stdout + r.stderr)

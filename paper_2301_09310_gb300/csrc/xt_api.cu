@@ -30,6 +30,7 @@ struct GraphEntry {
   cudaGraphExec_t exec = nullptr;
 };
 constexpr int kDescSlots = 64;   // pinned staging slots for the per-call descriptor
+constexpr int kMaxBranches = 8;  // streams the DP launches of one call fork onto
 }  // namespace
 
 struct xt_ctx {
@@ -60,6 +61,11 @@ struct xt_ctx {
   // CUDA graphs of whole calls
   bool graphs = true;
   cudaStream_t cap_stream = nullptr;
+  // the DP launches of a call fork onto these streams and join back
+  int branches = kMaxBranches;
+  cudaStream_t aux[kMaxBranches] = {};
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev[kMaxBranches] = {};
   std::vector<GraphEntry> graph_cache;
   int match = 1;                 // scoring of the call being planned
   int forced_P = 0;              // schedule override (0: per-bucket table)
@@ -150,7 +156,10 @@ void drop_graphs(xt_ctx* ctx) {
   ctx->graph_cache.clear();
 }
 
-// Carve the per-call workspace for n pairs (and the device batch descriptor).
+// Carve the per-call workspace for up to n pairs (and the device batch
+// descriptor).  Calls pass their capacity class n_cap, not their own n: the
+// region offsets then depend only on the class, so a graph captured for one
+// call of a class stays valid for every other call of that class.
 xt_status get_work(xt_ctx* ctx, int32_t n, Work* w, Batch** desc) {
   size_t off = 0;
   const size_t o_desc = off; off = align_up(off + sizeof(Batch));
@@ -370,11 +379,28 @@ cudaError_t enqueue(xt_ctx* ctx, bool plain, const Plan& pl, int plain_rs, const
     e = launch_plain(desc, n_cap, sc, w, plain_rs, stream);
     ++dp;
   }
-  for (int i = 0; e == cudaSuccess && i < pl.n_launch; ++i) {
+  // The DP launches are independent (each drains its own bucket range), so
+  // they fork onto the auxiliary streams: a launch's tail overlaps the next
+  // launch's start, and small batches fill the GPU.  Launches on the shared
+  // global ring pool stay in order on branch 0.
+  const int nb = std::min(ctx->branches, pl.n_launch);
+  if (e == cudaSuccess && nb > 1) {
+    e = cudaEventRecord(ctx->fork_ev, stream);
+    for (int b = 0; e == cudaSuccess && b < nb; ++b) e = cudaStreamWaitEvent(ctx->aux[b], ctx->fork_ev, 0);
+  }
+  for (int i = 0, rr = 0; e == cudaSuccess && i < pl.n_launch; ++i) {
     const Launch& L = pl.launch[i];
-    e = L.lane ? launch_lane(desc, sc, w, L, i, ctx->pool, stream)
-               : launch_queue(desc, sc, w, L, i, ctx->pool, stream);
+    cudaStream_t st = stream;
+    if (nb > 1) st = ctx->aux[L.global_ring ? 0 : (rr++ % nb)];
+    e = L.lane ? launch_lane(desc, sc, w, L, i, ctx->pool, st)
+               : launch_queue(desc, sc, w, L, i, ctx->pool, st);
     ++dp;
+  }
+  if (e == cudaSuccess && nb > 1) {
+    for (int b = 0; e == cudaSuccess && b < nb; ++b) {
+      e = cudaEventRecord(ctx->join_ev[b], ctx->aux[b]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, ctx->join_ev[b], 0);
+    }
   }
   if (e == cudaSuccess && timed) {
     cudaEventRecord(ctx->ev[slot][1], stream);
@@ -395,9 +421,12 @@ xt_status run(xt_ctx* ctx, bool plain, const uint8_t* q_seq, int64_t q_bytes, co
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
   const Score sc = make_score(scr);
+  int n_cap_log2 = 10;
+  while ((1 << n_cap_log2) < n) ++n_cap_log2;
+  const int32_t n_cap = n_cap_log2 >= 31 ? INT32_MAX : (1 << n_cap_log2);
   Work w;
   Batch* desc = nullptr;
-  s = get_work(ctx, n, &w, &desc);
+  s = get_work(ctx, n_cap, &w, &desc);
   if (s != XT_OK) return s;
   Plan pl;
   int plain_rs = 0;
@@ -424,9 +453,6 @@ xt_status run(xt_ctx* ctx, bool plain, const uint8_t* q_seq, int64_t q_bytes, co
   e = cudaMemcpyAsync(desc, &ctx->desc_host[slot], sizeof(Batch), cudaMemcpyHostToDevice, stream);
   if (e == cudaSuccess) e = cudaEventRecord(ctx->desc_ev[slot], stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "descriptor copy");
-  int n_cap_log2 = 10;
-  while ((1 << n_cap_log2) < n) ++n_cap_log2;
-  const int32_t n_cap = n_cap_log2 >= 31 ? INT32_MAX : (1 << n_cap_log2);
   int dp = 0;
   GraphEntry* ge = nullptr;
   if (ctx->graphs && !ctx->timing) {
@@ -504,6 +530,11 @@ xt_status xt_ctx_create(xt_ctx** out, int device, size_t mem_budget_bytes) {
   for (int k = 0; ok && k < kDescSlots; ++k)
     ok = cudaEventCreateWithFlags(&c->desc_ev[k], cudaEventDisableTiming) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) == cudaSuccess;
+  for (int b = 0; ok && b < kMaxBranches; ++b) {
+    ok = cudaStreamCreateWithFlags(&c->aux[b], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->join_ev[b], cudaEventDisableTiming) == cudaSuccess;
+  }
   if (!ok) {
     cudaGetLastError();
     xt_ctx_destroy(c);
@@ -528,6 +559,11 @@ xt_status xt_ctx_destroy(xt_ctx* ctx) {
     if (e) cudaEventDestroy(e);
   if (ctx->desc_host) cudaFreeHost(ctx->desc_host);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+  for (int b = 0; b < kMaxBranches; ++b) {
+    if (ctx->aux[b]) cudaStreamDestroy(ctx->aux[b]);
+    if (ctx->join_ev[b]) cudaEventDestroy(ctx->join_ev[b]);
+  }
   delete ctx;
   return XT_OK;
 }
@@ -620,6 +656,14 @@ xt_status xt_ctx_set_graphs(xt_ctx* ctx, int enable) {
   return XT_OK;
 }
 
+xt_status xt_ctx_set_streams(xt_ctx* ctx, int branches) {
+  if (!ctx || branches < 1 || branches > kMaxBranches) return XT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (ctx->branches != branches) drop_graphs(ctx);
+  ctx->branches = branches;
+  return XT_OK;
+}
+
 xt_status xt_ctx_set_timing(xt_ctx* ctx, int enable) {
   if (!ctx) return XT_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
@@ -662,6 +706,8 @@ xt_status xt_ctx_set_schedule(xt_ctx* ctx, int P, int R) {
   ctx->forced_R = R;
   return XT_OK;
 }
+
+xt_status xt_scoring_check(const xt_scoring* sc) { return scoring_ok(sc) ? XT_OK : XT_EINVAL; }
 
 const char* xt_status_str(xt_status s) {
   switch (s) {

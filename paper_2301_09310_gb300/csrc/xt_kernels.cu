@@ -205,6 +205,9 @@ __global__ void __launch_bounds__(kQueueThreads)
     if (P > 1) idx = __shfl_sync(gmask, idx, 0, P);
     if (idx >= end) break;
     const int32_t k = w.order[idx];
+    // an index outside the batch would mean a corrupt workspace: skip it
+    // (group-uniform) rather than read outside the caller's arrays
+    if ((uint32_t)k >= (uint32_t)b.n) continue;
     const Pair pr = load_pair(b, k);
     const Outcome o = run_pair<P, R, WIDE>(pr, sc, s_prof, ring, stride, rmask, p, gmask);
     if (p == 0) write_result(b, k, o.score, o.qle, o.tle, o.gscore, o.gtle, o.max_off, XT_OK,
@@ -256,11 +259,12 @@ __global__ void __launch_bounds__(kLaneThreads, 4)
     base = begin + __shfl_sync(0xffffffffu, base, 0);
     if (base >= end) break;
     const int32_t idx = base + lane;
-    const bool valid = idx < end;
     Pair pr;
-    int32_t k = 0;
+    int32_t k = idx < end ? w.order[idx] : -1;
+    // an index outside the batch would mean a corrupt workspace: the lane
+    // idles rather than read outside the caller's arrays
+    const bool valid = (uint32_t)k < (uint32_t)b.n;
     if (valid) {
-      k = w.order[idx];
       pr = load_pair(b, k);
     } else {
       pr.q = b.q_seq; pr.t = b.t_seq; pr.qlen = 0; pr.tlen = 0; pr.h0 = 1;

@@ -224,3 +224,59 @@ def generate(wl: Workload, n: int | None = None, first: int = 0,
 
 def with_n(wl: Workload, n: int) -> Workload:
     return replace(wl, n_pairs=int(n))
+
+
+@dataclass
+class RequestStream:
+    """A served stream cut from one Batch: request r holds the consecutive
+    pairs [start[r], start[r] + size[r]) and arrives at arrival_s[r] seconds
+    after the stream starts.  q_rel/t_rel are the pairs' offsets relative to
+    the first base of their own request, so a request's arrays are views."""
+    batch: Batch
+    start: np.ndarray
+    size: np.ndarray
+    arrival_s: np.ndarray
+    q_rel: np.ndarray
+    t_rel: np.ndarray
+
+    def request(self, r: int):
+        """(q_seq, q_off, q_len, t_seq, t_off, t_len, h0) of request r, as views."""
+        b = self.batch
+        a, n = int(self.start[r]), int(self.size[r])
+        if n == 0:
+            e8, e64, e32 = np.empty(0, np.uint8), np.empty(0, np.int64), np.empty(0, np.int32)
+            return e8, e64, e32, e8, e64, e32, e32
+        qa, ta = int(b.q_off[a]), int(b.t_off[a])
+        qe = int(b.q_off[a + n - 1]) + int(b.q_len[a + n - 1])
+        te = int(b.t_off[a + n - 1]) + int(b.t_len[a + n - 1])
+        s = slice(a, a + n)
+        return (b.q_seq[qa:qe], self.q_rel[s], b.q_len[s], b.t_seq[ta:te], self.t_rel[s],
+                b.t_len[s], b.h0[s])
+
+
+def request_stream(b: Batch, rate_pairs_per_s: float, max_request: int = 4096,
+                   seed: int = 5, sizes=None) -> RequestStream:
+    """Cut b into requests of U[1, max_request] pairs (or the given sizes,
+    which must sum to b.n) with Poisson arrivals at an offered load of
+    rate_pairs_per_s (exponential gaps between requests, mean request size /
+    rate)."""
+    rng = np.random.default_rng(seed)
+    if sizes is None:
+        sizes = []
+        left = b.n
+        while left > 0:
+            k = int(min(left, rng.integers(1, max_request + 1)))
+            sizes.append(k)
+            left -= k
+    size = np.asarray(sizes, np.int64)
+    if int(size.sum()) != b.n or np.any(size < 0):
+        raise ValueError("request sizes must be >= 0 and sum to the batch's pairs")
+    start = np.zeros(size.size, np.int64)
+    if size.size > 1:
+        np.cumsum(size[:-1], out=start[1:])
+    mean_gap = (max_request + 1) / 2.0 / float(rate_pairs_per_s)
+    arrival = np.cumsum(rng.exponential(mean_gap, size.size))
+    nz = size > 0
+    q_rel = b.q_off - np.repeat(b.q_off[start[nz]], size[nz])
+    t_rel = b.t_off - np.repeat(b.t_off[start[nz]], size[nz])
+    return RequestStream(b, start, size, arrival, q_rel, t_rel)

@@ -162,8 +162,11 @@ def test_graph_replay_matches_direct(ctx):
     # the graph; each call brings its own arrays through the device descriptor
     import paper_2301_09310_gb300 as xt
     wl = synth.WORKLOADS["c3_mixed"]
-    batches = [synth.generate(wl, n=n, first=f) for n, f in
-               ((3000, 0), (2900, 10000), (2048, 20000), (3000, 30000), (1500, 40000))]
+    # sizes grow within a capacity class after its capture (2200 -> 4000 in
+    # the 4096 class, 1100 -> 2048 in the 2048 class): the workspace layout
+    # baked into a graph must hold every size of its class
+    sizes = (2100, 2200, 4000, 3000, 1500, 1100, 2048, 1025, 4096)
+    batches = [synth.generate(wl, n=n, first=10000 * k) for k, n in enumerate(sizes)]
     want = []
     direct = xt.Context(0)
     direct.set_graphs(False)
@@ -176,5 +179,5 @@ def test_graph_replay_matches_direct(ctx):
     for rep in range(2):
         for b, w in zip(batches, want):
             assert_same(run_gpu(ctx, b, wl.scoring), w, f"graph replay {rep}")
-    for b in batches[:2]:
+    for b in batches[2:4]:
         assert_same(run_gpu(ctx, b, wl.scoring), run_oracle(b, wl.scoring), "graph vs oracle")
