@@ -71,6 +71,8 @@ def parse_args():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-pairs", type=int, default=4_000_000,
                     help="pairs of the c5 stream per offered-load level")
+    ap.add_argument("--tune", choices=["auto", "off"], default="auto",
+                    help="auto: autotune the workload's length buckets before warm-up")
     ap.add_argument("--streams", type=int, default=0,
                     help="streams the extension kernels of a call fork onto (0: library default)")
     ap.add_argument("--serve-slots", type=int, default=3)
@@ -283,6 +285,14 @@ def run_xt(args):
     if args.streams:
         ctx.set_streams(args.streams)
     stream = torch.cuda.current_stream(dev)
+    tuning = None
+    j_max = max(5, int(np.ceil(np.log2(int(b.q_len.max()) + 2))))
+    if args.tune == "auto":
+        t0 = time.perf_counter()
+        ctx.autotune(wl.scoring, j_max=j_max)
+        tuning = {"seconds": round(time.perf_counter() - t0, 2),
+                  "schedule": {f"j{j}": "P{}R{}".format(*ctx.bucket_schedule(wl.scoring.w, j))
+                               for j in range(5, j_max + 1)}}
 
     def step(plain=False):
         ctx.extend(*d, wl.scoring, plain=plain, out=out, cells=cells, stream=stream)
@@ -348,6 +358,7 @@ def run_xt(args):
                      "packed_cell_fraction": round(packed_frac, 4),
                      "peak_basis": "issue peak, derived: 152 SMs x 128 lanes x 2070 MHz (max clock)"},
         "clocks": clocks,
+        "tuning": tuning or "built-in schedule",
     }
     if not args.no_plain:
         step(plain=True)

@@ -204,6 +204,46 @@ xt_status xt_ctx_stats(xt_ctx* ctx, xt_stats* out);
 #define XT_MAX_BRANCHES 8
 xt_status xt_ctx_set_streams(xt_ctx* ctx, int branches);
 
+/*
+ * Per-bucket schedules of the batched path.  The batch is bucketed by query
+ * length: bucket j (5..21) holds queries of 2^(j-1) - 1 .. 2^j - 2 bases
+ * (bucket 5 also the shorter ones).  A schedule runs a bucket with P lanes
+ * per pair and R rows per lane: P = 1 is the one-lane engine (one thread per
+ * pair, R = 4, 8 or 16; packed 16-bit where exact), P = 2..32 the group
+ * engine (P lanes of a warp per pair, R = 4 or 8, or 16 with P <= 4).
+ * Schedules are kept per band w: a call uses the schedules set for its own
+ * scoring's w and the built-in rule for buckets without one.  P = 0 removes
+ * a bucket's schedule.  XT_EINVAL if (P, R) does not exist or its band ring
+ * does not fit on this device.  Results never depend on the schedule.
+ */
+xt_status xt_ctx_set_bucket_schedule(xt_ctx* ctx, int w, int j, int P, int R);
+/* The schedule set for (w, j): *P = 0 when the built-in rule applies. */
+xt_status xt_ctx_get_bucket_schedule(xt_ctx* ctx, int w, int j, int* P, int* R);
+
+/*
+ * Autotuner.  For every bucket j = 5..j_max, times each available (P, R) on
+ * synthetic pairs of that bucket's lengths (each query a mutated copy of its
+ * target, so pairs extend over the full band) with the scoring `sc`, and
+ * keeps the fastest as the bucket's schedule for sc->w on this context.  A
+ * trial batch holds enough pairs to fill the GPU four times over with the
+ * one-lane engine (throughput at saturation), but at most about
+ * cells_per_trial useful cells (0 = 3e10).  When
+ * table_path is not NULL the schedules are also written to that JSON file
+ * (entries of other devices or bands in it are kept), for
+ * xt_ctx_load_tuning.  Every schedule tried must give bit-identical results
+ * on the tuning pairs (XT_ECUDA otherwise).  Needs the global override of
+ * xt_ctx_set_schedule off (XT_EINVAL).  Synchronous; takes seconds.
+ */
+xt_status xt_autotune(xt_ctx* ctx, const xt_scoring* sc, int j_max, double cells_per_trial,
+                      const char* table_path);
+
+/*
+ * Load the schedules a table written by xt_autotune holds for this
+ * context's device (same name and SM count); entries of other devices are
+ * ignored.  XT_EINVAL if the file cannot be read or parsed.
+ */
+xt_status xt_ctx_load_tuning(xt_ctx* ctx, const char* table_path);
+
 /* XT_OK if the scoring record is within the ranges above, else XT_EINVAL. */
 xt_status xt_scoring_check(const xt_scoring* sc);
 

@@ -25,7 +25,9 @@ EXPORTED = ("xt_ctx_create", "xt_ctx_destroy", "xt_ctx_sync", "xt_extend_batch",
             "xt_ctx_last_error", "xt_ctx_set_schedule", "xt_ctx_set_timing", "xt_ctx_stats",
             "xt_extend_batch_static", "xt_ctx_set_graphs", "xt_scoring_check", "xt_now_ns",
             "xt_serve_create", "xt_serve_submit", "xt_serve_poll", "xt_serve_wait",
-            "xt_serve_pause", "xt_serve_get_stats", "xt_serve_destroy", "xt_ctx_set_streams")
+            "xt_serve_pause", "xt_serve_get_stats", "xt_serve_destroy", "xt_ctx_set_streams",
+            "xt_ctx_set_bucket_schedule", "xt_ctx_get_bucket_schedule", "xt_autotune",
+            "xt_ctx_load_tuning")
 XT_STATIC_MAX_PAIRS = 1 << 20
 
 
@@ -104,6 +106,17 @@ def load_library(path: str | None = None):
     lib.xt_extend_batch_static.restype = ctypes.c_int
     lib.xt_ctx_set_graphs.argtypes = [P, ctypes.c_int]
     lib.xt_ctx_set_graphs.restype = ctypes.c_int
+    lib.xt_ctx_set_bucket_schedule.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_int]
+    lib.xt_ctx_get_bucket_schedule.argtypes = [P, ctypes.c_int, ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_int),
+                                               ctypes.POINTER(ctypes.c_int)]
+    lib.xt_autotune.argtypes = [P, ctypes.POINTER(xt_scoring), ctypes.c_int, ctypes.c_double,
+                                ctypes.c_char_p]
+    lib.xt_ctx_load_tuning.argtypes = [P, ctypes.c_char_p]
+    for fn in ("xt_ctx_set_bucket_schedule", "xt_ctx_get_bucket_schedule", "xt_autotune",
+               "xt_ctx_load_tuning"):
+        getattr(lib, fn).restype = ctypes.c_int
     lib.xt_ctx_set_streams.argtypes = [P, ctypes.c_int]
     lib.xt_ctx_set_streams.restype = ctypes.c_int
     lib.xt_ctx_set_timing.argtypes = [P, ctypes.c_int]
@@ -125,7 +138,9 @@ def load_library(path: str | None = None):
     lib.xt_serve_get_stats.argtypes = [P, ctypes.POINTER(xt_serve_stats)]
     lib.xt_serve_destroy.argtypes = [P]
     for fn in ("xt_serve_create", "xt_serve_submit", "xt_serve_poll", "xt_serve_wait",
-               "xt_serve_pause", "xt_serve_get_stats", "xt_serve_destroy", "xt_ctx_set_streams"):
+               "xt_serve_pause", "xt_serve_get_stats", "xt_serve_destroy", "xt_ctx_set_streams",
+            "xt_ctx_set_bucket_schedule", "xt_ctx_get_bucket_schedule", "xt_autotune",
+            "xt_ctx_load_tuning"):
         getattr(lib, fn).restype = ctypes.c_int
     _LIB = lib
     return lib
@@ -154,6 +169,29 @@ def xt_ctx_set_schedule(ctx: int, P: int, R: int) -> int:
 
 def xt_ctx_set_graphs(ctx: int, enable: bool) -> int:
     return load_library().xt_ctx_set_graphs(ctypes.c_void_p(ctx), int(bool(enable)))
+
+
+def xt_ctx_set_bucket_schedule(ctx: int, w: int, j: int, P: int, R: int) -> int:
+    return load_library().xt_ctx_set_bucket_schedule(ctypes.c_void_p(ctx), int(w), int(j), int(P),
+                                                     int(R))
+
+
+def xt_ctx_get_bucket_schedule(ctx: int, w: int, j: int) -> tuple[int, int, int]:
+    P, R = ctypes.c_int(0), ctypes.c_int(0)
+    s = load_library().xt_ctx_get_bucket_schedule(ctypes.c_void_p(ctx), int(w), int(j),
+                                                  ctypes.byref(P), ctypes.byref(R))
+    return s, P.value, R.value
+
+
+def xt_autotune(ctx: int, sc, j_max: int = 14, cells_per_trial: float = 0.0,
+                table_path: str | None = None) -> int:
+    return load_library().xt_autotune(ctypes.c_void_p(ctx), ctypes.byref(_scoring(sc)), int(j_max),
+                                      float(cells_per_trial),
+                                      table_path.encode() if table_path else None)
+
+
+def xt_ctx_load_tuning(ctx: int, table_path: str) -> int:
+    return load_library().xt_ctx_load_tuning(ctypes.c_void_p(ctx), table_path.encode())
 
 
 def xt_ctx_set_streams(ctx: int, branches: int) -> int:
@@ -332,6 +370,23 @@ class Context:
 
     def set_graphs(self, enable: bool = True):
         self._check(xt_ctx_set_graphs(self.handle, enable), "xt_ctx_set_graphs")
+
+    def set_bucket_schedule(self, w: int, j: int, P: int, R: int = 8):
+        self._check(xt_ctx_set_bucket_schedule(self.handle, w, j, P, R),
+                    "xt_ctx_set_bucket_schedule")
+
+    def bucket_schedule(self, w: int, j: int) -> tuple[int, int]:
+        s, P, R = xt_ctx_get_bucket_schedule(self.handle, w, j)
+        self._check(s, "xt_ctx_get_bucket_schedule")
+        return P, R
+
+    def autotune(self, scoring, j_max: int = 14, cells_per_trial: float = 0.0,
+                 table_path: str | None = None):
+        self._check(xt_autotune(self.handle, scoring, j_max, cells_per_trial, table_path),
+                    "xt_autotune")
+
+    def load_tuning(self, table_path: str):
+        self._check(xt_ctx_load_tuning(self.handle, table_path), "xt_ctx_load_tuning")
 
     def set_streams(self, branches: int):
         self._check(xt_ctx_set_streams(self.handle, branches), "xt_ctx_set_streams")

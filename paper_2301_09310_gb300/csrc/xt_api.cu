@@ -8,78 +8,17 @@
 #include <vector>
 
 #include "xt.h"
+#include "xt_ctx.cuh"
 #include "xt_kernels.cuh"
 
 using namespace xt;
-
-namespace {
-// A captured call: same scoring, schedule, capacity class and workspace.
-struct GraphKey {
-  int plain;
-  xt_scoring sc;
-  int forced_P, forced_R;
-  int n_cap_log2;
-  void* work;
-  void* pool;
-  bool has_cells;
-  bool operator==(const GraphKey& o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
-};
-struct GraphEntry {
-  GraphKey key;
-  int seen = 0;                   // calls with this key (captured on the second)
-  cudaGraphExec_t exec = nullptr;
-};
-constexpr int kDescSlots = 64;   // pinned staging slots for the per-call descriptor
-constexpr int kMaxBranches = 8;  // streams the DP launches of one call fork onto
-}  // namespace
-
-struct xt_ctx {
-  int device = 0;
-  int num_sms = 0;
-  int smem_optin = 0;
-  size_t budget = 0;            // 0: no cap
-  size_t held = 0;              // bytes of device memory held
-  // per-call workspace (grown on demand)
-  void* work = nullptr;
-  size_t work_bytes = 0;
-  // global ring pool for pairs whose band does not fit in shared memory
-  int2* pool = nullptr;
-  size_t pool_bytes = 0;
-  // end-to-end staging: device copies of host inputs and pinned host mirrors
-  void* dev_in = nullptr;
-  size_t dev_in_bytes = 0;
-  // launch accounting and DP timing (xt_ctx_stats)
-  bool timing = false;
-  static constexpr int kEvRing = 256;
-  cudaEvent_t ev[kEvRing][2] = {};
-  int ev_pending = 0;
-  int calls = 0, launches = 0, dp_launches = 0;
-  // per-call batch descriptor: pinned host slots copied to a device slot
-  xt::Batch* desc_host = nullptr;
-  cudaEvent_t desc_ev[kDescSlots] = {};
-  int desc_next = 0;
-  // CUDA graphs of whole calls
-  bool graphs = true;
-  cudaStream_t cap_stream = nullptr;
-  // the DP launches of a call fork onto these streams and join back
-  int branches = kMaxBranches;
-  cudaStream_t aux[kMaxBranches] = {};
-  cudaEvent_t fork_ev = nullptr;
-  cudaEvent_t join_ev[kMaxBranches] = {};
-  std::vector<GraphEntry> graph_cache;
-  int match = 1;                 // scoring of the call being planned
-  int forced_P = 0;              // schedule override (0: per-bucket table)
-  int forced_R = 0;
-  std::mutex mu;
-  std::string last_error;
-};
 
 namespace {
 
 constexpr size_t kAlign = 256;
 constexpr int kPlainRsCapLog2 = 13;    // plain kernel ring up to 8192 entries (64 KB)
 constexpr int kQueueRsCapLog2 = 12;    // queue kernels: ring up to 4096 entries per group
-constexpr size_t kPoolCap = 512u << 20;
+constexpr size_t kPoolCap = (size_t)2 << 30;  // global ring pool cap (allocated only when a plan needs it)
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -150,11 +89,15 @@ xt_status dev_alloc(xt_ctx* ctx, void** p, size_t* have, size_t want) {
   return XT_OK;
 }
 
-void drop_graphs(xt_ctx* ctx) {
+}  // namespace
+
+void xt::drop_graphs(xt_ctx* ctx) {
   for (auto& g : ctx->graph_cache)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   ctx->graph_cache.clear();
 }
+
+namespace {
 
 // Carve the per-call workspace for up to n pairs (and the device batch
 // descriptor).  Calls pass their capacity class n_cap, not their own n: the
@@ -199,7 +142,32 @@ int64_t next_pow2(int64_t x) { return (int64_t)1 << log2_ceil(x); }
 // Schedule of bucket j (queries of qlen + 2 <= 2^j): the fewest lanes per pair
 // whose shared-memory ring fits 32 KB per CTA.  The ring needs
 // min(qlen, P*R + 2w) + 2 entries.
+// The tuned schedule of bucket j for band w, or nullptr (built-in rule).
+const BucketSched* tuned(const xt_ctx* ctx, int w, int j) {
+  if (ctx->forced_P) return nullptr;
+  for (const auto& t : ctx->tuning)
+    if (t.w == w && t.b[j].P > 0) return &t.b[j];
+  return nullptr;
+}
+
+// Ring entries (log2) of a group-engine pair of bucket j under band w.
+int queue_ring_log2(int j, int w, int P, int R) {
+  return log2_ceil(std::min<int64_t>((int64_t)1 << j, next_pow2((int64_t)P * R + 2 * (int64_t)w + 2)));
+}
+
+bool queue_instantiated(int P, int R) {
+  if (R == 4 || R == 8) return P == 1 || P == 2 || P == 4 || P == 8 || P == 16 || P == 32;
+  if (R == 16) return P == 1 || P == 2 || P == 4;
+  return false;
+}
+
 void bucket_schedule(const xt_ctx* ctx, int j, int w, int* P, int* R, int* rs_log2, bool* huge) {
+  if (const BucketSched* t = tuned(ctx, w, j)) {
+    if (t->P > 1) {
+      *P = t->P; *R = t->R; *rs_log2 = queue_ring_log2(j, w, t->P, t->R); *huge = false;
+      return;
+    }
+  }
   if (ctx->forced_P > 1) {
     const int64_t need = std::min<int64_t>(
         (int64_t)1 << j, next_pow2((int64_t)ctx->forced_P * ctx->forced_R + 2 * (int64_t)w + 2));
@@ -242,7 +210,8 @@ constexpr size_t kLaneSmemCap = 48 * 1024;
 // One-lane launch of bucket j for class cls (PACKED or NARROW); false if it
 // needs a global ring and those are not allowed.
 bool lane_launch(xt_ctx* ctx, const Score& sc, int cls, int j, bool allow_gring, Launch* L) {
-  const int R = ctx->forced_P == 1 ? ctx->forced_R : 8;
+  const BucketSched* t = tuned(ctx, sc.w, j);
+  const int R = ctx->forced_P == 1 ? ctx->forced_R : (t && t->P == 1 ? t->R : 8);
   const int rows = cls == CLS_PACKED ? 2 * R : R;
   const int64_t need = std::min<int64_t>((int64_t)1 << j, next_pow2(rows + 2 * (int64_t)sc.w + 2));
   const int lg = log2_ceil(need);
@@ -271,7 +240,8 @@ void plan_batched(xt_ctx* ctx, const Score& sc, Plan* pl, bool allow_gring = tru
   bool lane_j[kNumJ] = {false};
   for (int j = kJMin; j <= kJMax; ++j) {
     Launch L;
-    const bool want = ctx->forced_P == 1 || (!ctx->forced_P && j <= kLaneJMax);
+    const BucketSched* t = tuned(ctx, sc.w, j);
+    const bool want = ctx->forced_P == 1 || (!ctx->forced_P && (t ? t->P == 1 : j <= kLaneJMax));
     lane_j[j] = want &&
                 lane_launch(ctx, sc, CLS_PACKED, j, allow_gring, &L) &&
                 lane_launch(ctx, sc, CLS_NARROW, j, allow_gring, &L);
@@ -327,6 +297,24 @@ size_t pool_bytes(const Plan& pl) {
   }
   return need;
 }
+
+}  // namespace
+
+bool xt::bucket_sched_ok(const xt_ctx* ctx, int w, int j, int P, int R) {
+  if (j < kJMin || j > kJMax || w < 0) return false;
+  if (P == 1) {
+    if (R != 4 && R != 8 && R != 16) return false;
+    // one-lane rings beyond shared memory go to the global pool: keep it bounded
+    const int64_t need = std::min<int64_t>((int64_t)1 << j, next_pow2(2 * R + 2 * (int64_t)w + 2));
+    const size_t per_cta = (size_t)kLaneThreads * lane_ring_bytes(CLS_NARROW, log2_ceil(need));
+    return per_cta <= kLaneSmemCap || per_cta * 4 * (size_t)ctx->num_sms <= kPoolCap;
+  }
+  if (!queue_instantiated(P, R)) return false;
+  const int lg = queue_ring_log2(j, w, P, R);
+  return lg <= kQueueRsCapLog2 && queue_smem_bytes(P, lg) <= (size_t)ctx->smem_optin - 1024;
+}
+
+namespace {
 
 void plan_plain(xt_ctx* ctx, const Score& sc, Plan* pl, int* rs_log2) {
   const int64_t need = 256 + 2 * (int64_t)sc.w + 2;
@@ -653,6 +641,40 @@ xt_status xt_ctx_set_graphs(xt_ctx* ctx, int enable) {
   if (!ctx) return XT_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   ctx->graphs = enable != 0;
+  return XT_OK;
+}
+
+xt_status xt_ctx_set_bucket_schedule(xt_ctx* ctx, int w, int j, int P, int R) {
+  if (!ctx || w < 0 || j < kJMin || j > kJMax) return XT_EINVAL;
+  const int wc = w > 2 * XT_MAX_LEN ? 2 * XT_MAX_LEN : w;  // the band the plan sees
+  if (P != 0 && !bucket_sched_ok(ctx, wc, j, P, R))
+    return fail(ctx, XT_EINVAL, "schedule not available for this bucket and band");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  TuneEntry* e = nullptr;
+  for (auto& t : ctx->tuning)
+    if (t.w == wc) e = &t;
+  if (!e) {
+    ctx->tuning.push_back(TuneEntry());
+    e = &ctx->tuning.back();
+    e->w = wc;
+  }
+  e->b[j].P = P;
+  e->b[j].R = P ? R : 0;
+  drop_graphs(ctx);
+  return XT_OK;
+}
+
+xt_status xt_ctx_get_bucket_schedule(xt_ctx* ctx, int w, int j, int* P, int* R) {
+  if (!ctx || !P || !R || w < 0 || j < kJMin || j > kJMax) return XT_EINVAL;
+  const int wc = w > 2 * XT_MAX_LEN ? 2 * XT_MAX_LEN : w;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  *P = 0;
+  *R = 0;
+  for (auto& t : ctx->tuning)
+    if (t.w == wc) {
+      *P = t.b[j].P;
+      *R = t.b[j].R;
+    }
   return XT_OK;
 }
 

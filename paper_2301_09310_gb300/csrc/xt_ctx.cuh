@@ -1,0 +1,93 @@
+// xt_ctx.cuh -- the library context (xt_ctx of include/xt.h) and the
+// per-bucket schedule table, shared by the API and the autotuner.
+#pragma once
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "xt.h"
+#include "xt_kernels.cuh"
+
+namespace xt {
+
+// A captured call: same scoring, schedule, capacity class and workspace.
+struct GraphKey {
+  int plain;
+  xt_scoring sc;
+  int forced_P, forced_R;
+  int n_cap_log2;
+  void* work;
+  void* pool;
+  bool has_cells;
+  bool operator==(const GraphKey& o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
+};
+struct GraphEntry {
+  GraphKey key;
+  int seen = 0;                   // calls with this key (captured on the second)
+  cudaGraphExec_t exec = nullptr;
+};
+constexpr int kDescSlots = 64;   // pinned staging slots for the per-call descriptor
+constexpr int kMaxBranches = 8;  // streams the DP launches of one call fork onto
+
+// Schedule of one length bucket: P lanes per pair (1: the one-lane engine),
+// R rows per lane.  P = 0: the built-in rule.
+struct BucketSched {
+  int P = 0, R = 0;
+};
+// The schedules of every bucket for calls whose band is w.
+struct TuneEntry {
+  int w = 0;
+  BucketSched b[kNumJ];
+};
+
+// Whether (P, R) is an instantiated schedule whose ring fits for bucket j
+// under band w on this context's device.
+bool bucket_sched_ok(const struct ::xt_ctx* ctx, int w, int j, int P, int R);
+// Drop every captured graph of the context.
+void drop_graphs(struct ::xt_ctx* ctx);
+
+}  // namespace xt
+
+struct xt_ctx {
+  int device = 0;
+  int num_sms = 0;
+  int smem_optin = 0;
+  size_t budget = 0;            // 0: no cap
+  size_t held = 0;              // bytes of device memory held
+  // per-call workspace (grown on demand)
+  void* work = nullptr;
+  size_t work_bytes = 0;
+  // global ring pool for pairs whose band does not fit in shared memory
+  int2* pool = nullptr;
+  size_t pool_bytes = 0;
+  // end-to-end staging: device copies of host inputs and pinned host mirrors
+  void* dev_in = nullptr;
+  size_t dev_in_bytes = 0;
+  // launch accounting and DP timing (xt_ctx_stats)
+  bool timing = false;
+  static constexpr int kEvRing = 256;
+  cudaEvent_t ev[kEvRing][2] = {};
+  int ev_pending = 0;
+  int calls = 0, launches = 0, dp_launches = 0;
+  // per-call batch descriptor: pinned host slots copied to a device slot
+  xt::Batch* desc_host = nullptr;
+  cudaEvent_t desc_ev[xt::kDescSlots] = {};
+  int desc_next = 0;
+  // CUDA graphs of whole calls
+  bool graphs = true;
+  cudaStream_t cap_stream = nullptr;
+  // the DP launches of a call fork onto these streams and join back
+  int branches = xt::kMaxBranches;
+  cudaStream_t aux[xt::kMaxBranches] = {};
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev[xt::kMaxBranches] = {};
+  std::vector<xt::GraphEntry> graph_cache;
+  int match = 1;                 // scoring of the call being planned
+  int forced_P = 0;              // schedule override (0: per-bucket table)
+  int forced_R = 0;
+  std::vector<xt::TuneEntry> tuning;  // per-band bucket schedules (xt_autotune)
+  std::mutex mu;
+  std::string last_error;
+};
+
