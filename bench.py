@@ -147,13 +147,30 @@ def barrier(world):
 
 
 def reduce(world, value, op):
+    """All-reduce one number across ranks (on the GPU under NCCL, on the host
+    under gloo): the timing max and the work sums of the weak-scaling line."""
     if world == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([float(value)], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def shard_of(rank: int, n_per_gpu: int) -> tuple[int, int]:
+    """Weak scaling: rank r extends pairs [r * n, (r + 1) * n) of the
+    workload's counter-based stream, so shards are disjoint and every rank's
+    pairs are the same whatever the number of ranks."""
+    return rank * n_per_gpu, n_per_gpu
+
+
+def aggregate(world, units_local: float, seconds_local: float):
+    """Whole-job throughput: units summed over ranks / the slowest rank's time."""
+    total = reduce(world, units_local, _sum_op() if world > 1 else None)
+    slowest = reduce(world, seconds_local, _max_op() if world > 1 else None)
+    return total, slowest, total / slowest
 
 
 def algorithmic_ops(b, cells, sc):
@@ -172,13 +189,17 @@ def algorithmic_ops(b, cells, sc):
     return float(ops), float(c[packed].sum() / max(c.sum(), 1.0))
 
 
+# the files that define the extension kernels' device code
+KERNEL_SOURCES = ("xt_common.cuh", "xt_engine.cuh", "xt_lane.cuh", "xt_kernels.cuh",
+                  "xt_kernels.cu")
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2301_09310_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(f.read())
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
@@ -275,7 +296,8 @@ def run_xt(args):
     xbuild.build()
     wl = synth.WORKLOADS[args.workload]
     n = args.pairs or wl.n_pairs
-    b = synth.generate(wl, n=n, first=rank * n)
+    first, n = shard_of(rank, n)
+    b = synth.generate(wl, n=n, first=first)
     dev = torch.device("cuda", local)
     T = lambda a: torch.from_numpy(a).to(dev)  # noqa: E731
     d = [T(b.q_seq), T(b.q_off), T(b.q_len), T(b.t_seq), T(b.t_off), T(b.t_len), T(b.h0)]
@@ -328,10 +350,10 @@ def run_xt(args):
     torch.cuda.synchronize()
     st = ctx.stats()
     ctx.set_timing(False)
-    ms_max = reduce(world, ms, _max_op())
-    total_cells = reduce(world, cells_step, _sum_op())
+    total_cells, s_max, cells_per_s = aggregate(world, cells_step, ms / 1e3)
+    ms_max = s_max * 1e3
     total_pairs = n * world
-    value = total_cells / (ms_max / 1e3) / 1e9
+    value = cells_per_s / 1e9
     dp_ms = st["dp_ms"] / max(1, st["timed_calls"])
     peak = SMS * LANES * MAX_MHZ * 1e6 / 1e12
     achieved = ops_step / (dp_ms / 1e3) / 1e12
