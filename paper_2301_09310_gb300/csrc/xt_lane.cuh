@@ -75,6 +75,14 @@ struct Query {
   }
 };
 
+// Unrolling of the fast-step loop of the packed engine (a tuning knob of the
+// build: the loop body is large, so unrolling trades register renaming of
+// the pipelined values against instruction-cache footprint).
+#ifndef XT_FAST_UNROLL_N
+#define XT_FAST_UNROLL_N 1
+#endif
+constexpr int kFastUnroll = XT_FAST_UNROLL_N;
+
 // ----------------------------------------------------------- 32-bit lane
 template <int R, bool MASKED>
 __device__ __forceinline__ void lane_step_i32(int32_t (&Hl)[R], int32_t (&HAl)[R],
@@ -152,16 +160,29 @@ __device__ __forceinline__ Outcome lane_pair_i32(const Pair& pr, bool valid, con
     else if (live) Hdiag = ring.at(lo - 1).x;
     const int32_t nsteps = live ? hi - lo + 1 : 0;
     const int32_t nmax = __reduce_max_sync(0xffffffffu, nsteps);
+    // the unmasked range: every live lane in its band body, every row in
+    // band, and the previous strip's row present at the column
+    constexpr int32_t kFar = 1 << 30;
+    int32_t sb_lo = 0, sb_hi = kFar;
+    if (live) {
+      sb_lo = max(0, R - 1 - w + i0 - lo);
+      sb_hi = min(hi - lo, w + i0 - lo);
+      if (i0 > 0) sb_hi = min(sb_hi, hi_prev - lo);
+      if (i0 + R > tlen) sb_hi = -1;
+    }
+    const int32_t fs = (int32_t)__reduce_max_sync(0xffffffffu, (uint32_t)sb_lo);
+    const int32_t fe = min(__reduce_min_sync(0xffffffffu, sb_hi), nmax - 1);
     const int32_t qlast = max(qlen - 1, 0);
     uint32_t code_n = live ? clamp_code(__ldg(pr.q + min(lo + 1, qlast))) : 0u;
     uint32_t prof_c = s_prof[live ? clamp_code(__ldg(pr.q + lo)) : 0u];
     int2 ring_c = live ? ring.at(lo) : make_int2(0, 0);
-    for (int32_t s = 0; s < nmax; ++s) {
+    int2 ring_n1 = live ? ring.at(lo + 1) : make_int2(0, 0);
+    auto slow_step = [&](int32_t s) {
       const int32_t c = lo + s;
       const bool act = live && c <= hi;
       const uint32_t code_nn = act ? clamp_code(__ldg(pr.q + min(c + 2, qlast))) : 0u;
       const uint32_t prof_n = s_prof[code_n];
-      const int2 ring_n = act ? ring.at(c + 1) : make_int2(0, 0);
+      const int2 ring_n2 = act ? ring.at(c + 2) : make_int2(0, 0);
       int32_t Hup = 0, Fup = 0;
       if (act) {
         if (i0 == 0) {
@@ -172,20 +193,50 @@ __device__ __forceinline__ Outcome lane_pair_i32(const Pair& pr, bool valid, con
         }
       }
       const int32_t d0 = c - i0;
-      const bool body = act && (d0 >= R - 1 - w) && (d0 <= w) && (i0 + R <= tlen);
       int32_t oH, oF;
-      if (__all_sync(0xffffffffu, body || !live)) {
-        lane_step_i32<R, false>(Hl, HAl, El, key, sel, prof_c, nnnn, Hdiag, Hup, Fup, c, alpha,
-                                beta, mc, 0, R - 1, oH, oF);
-      } else if (act) {
+      if (act)
         lane_step_i32<R, true>(Hl, HAl, El, key, sel, prof_c, nnnn, Hdiag, Hup, Fup, c, alpha,
                                beta, mc, d0 - w, min(d0 + w, tlen - 1 - i0), oH, oF);
-      }
       if (act) ring.at(c) = make_int2(oH, oF);
       Hdiag = Hup;
       prof_c = prof_n;
       code_n = code_nn;
-      ring_c = ring_n;
+      ring_c = ring_n1;
+      ring_n1 = ring_n2;
+    };
+    // nothing masked or checked; lanes without a pair compute on garbage and
+    // store only into their own ring, which they never read again
+    auto fast_step = [&](int32_t s) {
+      const int32_t c = lo + s;
+      const uint32_t code_nn = live ? clamp_code(__ldg(pr.q + min(c + 2, qlast))) : 0u;
+      const uint32_t prof_n = s_prof[code_n];
+      const int2 ring_n2 = ring.at(c + 2);
+      int32_t Hup, Fup;
+      if (i0 == 0) {
+        Hup = row_m1(c, h0, sc);
+        Fup = 0;
+      } else {
+        Hup = ring_c.x;
+        Fup = ring_c.y;
+      }
+      int32_t oH, oF;
+      lane_step_i32<R, false>(Hl, HAl, El, key, sel, prof_c, nnnn, Hdiag, Hup, Fup, c, alpha, beta,
+                              mc, 0, R - 1, oH, oF);
+      ring.at(c) = make_int2(oH, oF);
+      Hdiag = Hup;
+      prof_c = prof_n;
+      code_n = code_nn;
+      ring_c = ring_n1;
+      ring_n1 = ring_n2;
+    };
+    int32_t s = 0;
+    while (s < nmax) {
+      if (s >= fs && s <= fe) {
+        for (; s <= fe; ++s) fast_step(s);
+      } else {
+        slow_step(s);
+        ++s;
+      }
     }
     hi_prev = hi;
     if (live) {
@@ -340,7 +391,6 @@ __device__ __forceinline__ Outcome lane_pair_p16(const Pair& pr, bool valid, con
     if (!__any_sync(0xffffffffu, live)) break;
     uint32_t Hl[R], HAl[R], El[R], K[R], sel[R];
     int32_t Blo[R], Bhi[R];
-    uint32_t anyN = 0;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int32_t il = i0 + r, ih = i0 + R + r;
@@ -349,7 +399,6 @@ __device__ __forceinline__ Outcome lane_pair_p16(const Pair& pr, bool valid, con
       const uint32_t bl = cl & 3u, bh = 4u + (ch & 3u);
       const uint32_t nf = (cl == 4u ? 0x00FF0000u : 0u) | (ch == 4u ? 0xFF000000u : 0u);
       sel[r] = bl | ((bl | 8u) << 4) | (bh << 8) | ((bh | 8u) << 12) | nf;
-      anyN |= nf;
       // both strips start from column lo - 1 (column -1 when lo == 0)
       const int32_t hl = (lo == 0 && il < tlen) ? col_m1(il, h0, sc) : 0;
       const int32_t hh = (lo == 0 && ih < tlen) ? col_m1(ih, h0, sc) : 0;
@@ -360,7 +409,6 @@ __device__ __forceinline__ Outcome lane_pair_p16(const Pair& pr, bool valid, con
       Blo[r] = -1;
       Bhi[r] = -1;
     }
-    const bool has_n = __any_sync(0xffffffffu, anyN != 0);
     // lower strip's diagonal at its first column: H(i0-1, lo-1)
     int32_t dlo = 0;
     if (i0 == 0) dlo = h0;
@@ -378,6 +426,9 @@ __device__ __forceinline__ Outcome lane_pair_p16(const Pair& pr, bool valid, con
     if (live) {
       sb_lo = max(1, RR - w + i0 - lo);
       sb_hi = min(hi - lo, w + i0 - lo);
+      // the fast steps read the previous strip's row without checking that
+      // it reached the column
+      if (i0 > 0) sb_hi = min(sb_hi, hi_prev - lo);
       if (i0 + RR > tlen) sb_hi = -1;
     }
     const int32_t nmax = __reduce_max_sync(0xffffffffu, nsteps);
@@ -396,7 +447,9 @@ __device__ __forceinline__ Outcome lane_pair_p16(const Pair& pr, bool valid, con
     uint32_t ring_n2 = live ? ring.at(lo + 2) : 0u;
     int32_t blk = 0;     // steps taken in the current key block
     int32_t cbase = lo;  // lower strip's column at block step 0
-    auto step = [&](int32_t s, int mode) {
+    // A masked step: band edges, a lane whose lower strip has finished or
+    // whose upper strip has not started (those halves keep their state).
+    auto slow_step = [&](int32_t s) {
       const int32_t c = lo + s;
       const bool lo_act = live && c <= hi;
       const bool hi_act = live && s >= 1 && c - 1 <= hi;
@@ -414,28 +467,14 @@ __device__ __forceinline__ Outcome lane_pair_p16(const Pair& pr, bool valid, con
       const uint32_t D = prmt(tHF_prev, oH2, 0x5410u);
       const uint32_t pos2 = (uint32_t)blk * 0x00010001u;
       uint32_t oH, oF;
-      if (mode == 0) {
-        if (has_n)
-          lane_step_p16<R, false, true, false>(Hl, HAl, El, K, sel, prof, prof_prev, nn2, D, Hup,
-                                               Fup, pos2, na2, nb2, mcm, 0u, 0u, oH, oF);
-        else
-          lane_step_p16<R, false, false, false>(Hl, HAl, El, K, sel, prof, prof_prev, nn2, D, Hup,
-                                                Fup, pos2, na2, nb2, mcm, 0u, 0u, oH, oF);
-      } else {
-        const int32_t d0 = c - i0;
-        const int32_t dh = d0 - 1 - R;  // upper strip: column c-1 minus its first row
-        const uint32_t inband =
-            (lo_act ? bit_range(d0 - w, min(d0 + w, tlen - 1 - i0), R) : 0u) |
-            ((hi_act ? bit_range(dh - w, min(dh + w, tlen - 1 - i0 - R), R) : 0u) << 16);
-        if (mode == 2) {
-          const uint32_t keep = (lo_act ? 0u : 0x0000FFFFu) | (hi_act ? 0u : 0xFFFF0000u);
-          lane_step_p16<R, true, true, true>(Hl, HAl, El, K, sel, prof, prof_prev, nn2, D, Hup,
-                                             Fup, pos2, na2, nb2, mcm, inband, keep, oH, oF);
-        } else {
-          lane_step_p16<R, true, true, false>(Hl, HAl, El, K, sel, prof, prof_prev, nn2, D, Hup,
-                                              Fup, pos2, na2, nb2, mcm, inband, 0u, oH, oF);
-        }
-      }
+      const int32_t d0 = c - i0;
+      const int32_t dh = d0 - 1 - R;  // upper strip: column c-1 minus its first row
+      const uint32_t inband =
+          (lo_act ? bit_range(d0 - w, min(d0 + w, tlen - 1 - i0), R) : 0u) |
+          ((hi_act ? bit_range(dh - w, min(dh + w, tlen - 1 - i0 - R), R) : 0u) << 16);
+      const uint32_t keep = (lo_act ? 0u : 0x0000FFFFu) | (hi_act ? 0u : 0xFFFF0000u);
+      lane_step_p16<R, true, true, true>(Hl, HAl, El, K, sel, prof, prof_prev, nn2, D, Hup, Fup,
+                                         pos2, na2, nb2, mcm, inband, keep, oH, oF);
       if (hi_act) ring.at(c - 1) = prmt(oH, oF, 0x7632u);
       oH2 = oH1;
       oH1 = oH;
@@ -455,17 +494,63 @@ __device__ __forceinline__ Outcome lane_pair_p16(const Pair& pr, bool valid, con
         blk = 0;
       }
     };
-    // the first step (upper strip not started) and the steps past any lane's
-    // end (lower strip finished) keep state; the fast range never holds them
-    const int32_t nmin = __reduce_min_sync(0xffffffffu, live ? nsteps : kFar);
+    // A fast step: every live lane has both strips active, every row in band
+    // and the previous strip's row present at the column, so nothing is
+    // masked or checked; lanes without a pair compute on garbage and store
+    // only into their own ring, which they never read again.
+    auto fast_step = [&](int32_t s) {
+      const int32_t c = lo + s;
+      const uint32_t code_n4 = live ? qs.code(min(c + 4, qlast)) : 0u;
+      const uint32_t prof_n = s_prof[code_n1];
+      const uint32_t ring_n3 = ring.at(c + 3);
+      uint32_t tHF;
+      if (i0 == 0) tHF = live ? ((uint32_t)row_m1(c, h0, sc) & 0xFFFFu) : 0u;
+      else tHF = ring_c;
+      const uint32_t Hup = prmt(tHF, oH1, 0x5410u);
+      const uint32_t Fup = prmt(tHF, oF1, 0x5432u);
+      const uint32_t D = prmt(tHF_prev, oH2, 0x5410u);
+      const uint32_t pos2 = (uint32_t)blk * 0x00010001u;
+      // one code path with the N-base select (2 instructions per row) is
+      // faster than a vote between two copies of the step: the instruction
+      // cache, not the ALU count, decides here
+      uint32_t oH, oF;
+      lane_step_p16<R, false, true, false>(Hl, HAl, El, K, sel, prof_c, prof_prev, nn2, D, Hup,
+                                           Fup, pos2, na2, nb2, mcm, 0u, 0u, oH, oF);
+      ring.at(c - 1) = prmt(oH, oF, 0x7632u);
+      oH2 = oH1;
+      oH1 = oH;
+      oF1 = oF;
+      tHF_prev = tHF;
+      prof_prev = prof_c;
+      prof_c = prof_n;
+      code_n1 = code_n2;
+      code_n2 = code_n3;
+      code_n3 = code_n4;
+      ring_c = ring_n1;
+      ring_n1 = ring_n2;
+      ring_n2 = ring_n3;
+      ++blk;
+    };
+    // One loop, one call site per kind of step (the steps are large: code
+    // size matters more than the branch).  The fast range [fs, fe] never
+    // holds the first step (upper strip not started) or a step past any
+    // lane's end; it runs in stretches up to the next key-block boundary.
     int32_t s = 0;
-    step(s++, 2);
-    if (fs <= fe) {
-      for (; s < fs; ++s) step(s, 1);
-      for (; s <= fe; ++s) step(s, 0);
+    while (s < nmax) {
+      if (s >= fs && s <= fe) {
+        const int32_t e = min(fe, s + (kTagSteps - 1 - blk));
+#pragma unroll kFastUnroll
+        for (; s <= e; ++s) fast_step(s);
+        if (blk == kTagSteps) {
+          fold_keys<R>(K, Blo, Bhi, cbase);
+          cbase += kTagSteps;
+          blk = 0;
+        }
+      } else {
+        slow_step(s);
+        ++s;
+      }
     }
-    for (; s < nmin - 1 && s < nmax; ++s) step(s, 1);
-    for (; s < nmax; ++s) step(s, 2);
     fold_keys<R>(K, Blo, Bhi, cbase);
     hi_prev = hi;
     if (live) {
