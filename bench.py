@@ -69,6 +69,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-x2", action="store_true",
+                    help="skip the equal-length 5,000-pair calls of the paper's kernel comparison")
     ap.add_argument("--serve-pairs", type=int, default=4_000_000,
                     help="pairs of the c5 stream per offered-load level")
     ap.add_argument("--tune", choices=["auto", "off"], default="auto",
@@ -398,6 +400,8 @@ def run_xt(args):
         res["speedup_vs_plain"] = round(pms / ms, 3)
     if not args.no_e2e:
         res["e2e"] = e2e_leg(ctx, b, wl, args, dev, stream, world)
+    if not args.no_x2 and world == 1:
+        res["paper_x2"] = x2_leg(local, stream)
     if not args.no_serve and world == 1:
         res["serving"] = serve_leg(args, local, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -438,6 +442,76 @@ def e2e_leg(ctx, b, wl, args, dev, stream, world):
     return {"value": round(total_cells / dt / 1e9, 3), "unit": "GCUPS",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "ms_per_step": round(dt * 1e3, 3), "api": "xt_extend_batch_host (pinned host buffers)"}
+
+
+# The paper's only absolute kernel times for this comparison: 64 bp, 5,000 pairs
+# per call (Sec. V-B): SALoBa 0.51 ms on a GTX 1650 and 0.24 ms on an RTX 3090.
+PAPER_X2_MS = {64: {"GTX1650": 0.51, "RTX3090": 0.24}}
+X2_CANDIDATES = ((0, 0), (1, 8), (1, 16), (4, 8), (8, 8), (16, 8), (16, 4), (32, 8), (32, 4))
+
+
+def x2_leg(local, stream):
+    """Equal-length reads of the paper's kernel comparison (Sec. V-B): one
+    call of 5,000 pairs per length, unbanded (w = L), z-drop off.  These calls
+    are small and latency-bound, so each length times every schedule its
+    bucket can take on the batch itself and keeps the fastest (all of them
+    must give identical results); CUDA events around whole calls, averaged."""
+    import torch
+    import paper_2301_09310_gb300 as xt
+    from paper_2301_09310_gb300 import synth
+
+    dev = torch.device("cuda", local)
+    rows = []
+    for L in synth.X2_LENGTHS:
+        wl = synth.x2_workload(L)
+        b = synth.generate(wl)
+        d = [torch.from_numpy(a).to(dev) for a in
+             (b.q_seq, b.q_off, b.q_len, b.t_seq, b.t_off, b.t_len, b.h0)]
+        out = torch.empty((b.n, 7), dtype=torch.int32, device=dev)
+        cells = torch.empty(b.n, dtype=torch.int64, device=dev)
+        j = int(np.ceil(np.log2(L + 2)))
+        reps = 20 if L <= 512 else 4
+        best, first, agree = None, None, True
+        for P, R in X2_CANDIDATES:
+            ctx = xt.Context(local)
+            try:
+                if P:
+                    ctx.set_bucket_schedule(wl.scoring.w, j, P, R)
+            except xt.XtError:
+                ctx.close()
+                continue
+            for _ in range(3):
+                ctx.extend(*d, wl.scoring, out=out, cells=cells, stream=stream)
+            torch.cuda.synchronize()
+            got = (out.cpu().numpy(), cells.cpu().numpy())
+            if first is None:
+                first = got
+            elif not (np.array_equal(first[0], got[0]) and np.array_equal(first[1], got[1])):
+                agree = False
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                ctx.extend(*d, wl.scoring, out=out, cells=cells, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            ctx.close()
+            if best is None or ms < best[0]:
+                best = (ms, P, R)
+        useful = int(first[1].sum())
+        row = {"L": L, "pairs": b.n, "ms_per_call": round(best[0], 4),
+               "schedule": "built-in" if best[1] == 0 else f"P{best[1]}R{best[2]}",
+               "gcups": round(useful / (best[0] / 1e3) / 1e9, 2),
+               "table_gcups": round(b.n * L * L / (best[0] / 1e3) / 1e9, 2),
+               "schedules_agree": agree}
+        if L in PAPER_X2_MS:
+            row["paper_ms"] = PAPER_X2_MS[L]
+        rows.append(row)
+    return {"workload": "5,000 pairs per call, qlen = tlen = L, wgsim-like 2% substitutions and "
+                        "0.1% indels, w = L (whole table), z-drop off",
+            "timing": "CUDA events around whole xt_extend_batch calls, inputs resident",
+            "note": "paper times are other GPUs and full local (restarting) tables: context only",
+            "lengths": rows}
 
 
 def serve_leg(args, local, stream):

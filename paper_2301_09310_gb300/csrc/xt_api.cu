@@ -161,7 +161,8 @@ bool queue_instantiated(int P, int R) {
   return false;
 }
 
-void bucket_schedule(const xt_ctx* ctx, int j, int w, int* P, int* R, int* rs_log2, bool* huge) {
+void bucket_schedule(const xt_ctx* ctx, int j, int w, int* P, int* R, int* rs_log2, bool* huge,
+                     bool allow_gring = true) {
   if (const BucketSched* t = tuned(ctx, w, j)) {
     if (t->P > 1) {
       *P = t->P; *R = t->R; *rs_log2 = queue_ring_log2(j, w, t->P, t->R); *huge = false;
@@ -183,7 +184,11 @@ void bucket_schedule(const xt_ctx* ctx, int j, int w, int* P, int* R, int* rs_lo
     const int64_t need = std::min<int64_t>((int64_t)1 << j, next_pow2((int64_t)p * Rr + 2 * (int64_t)w + 2));
     const int lg = log2_ceil(need);
     const size_t bytes = queue_smem_bytes(p, lg);
-    if (bytes <= 32 * 1024 || (p == 32 && lg <= kQueueRsCapLog2)) {
+    // a ring that leaves room for fewer than two CTAs per SM runs better
+    // from the global slabs of the HUGE class (two CTAs per SM), where those
+    // are allowed
+    const size_t cap = allow_gring ? (size_t)ctx->smem_optin / 2 - 1024 : (size_t)ctx->smem_optin;
+    if (bytes <= 32 * 1024 || (p == 32 && lg <= kQueueRsCapLog2 && bytes <= cap)) {
       *P = p; *R = Rr; *rs_log2 = lg; *huge = false;
       return;
     }
@@ -257,7 +262,7 @@ void plan_batched(xt_ctx* ctx, const Score& sc, Plan* pl, bool allow_gring = tru
         if (cls == CLS_PACKED) { prev = -1; continue; }  // no packed pairs in this bucket
         int P, R, lg;
         bool huge;
-        bucket_schedule(ctx, j, sc.w, &P, &R, &lg, &huge);
+        bucket_schedule(ctx, j, sc.w, &P, &R, &lg, &huge, allow_gring);
         if (huge) {
           pl->jf.f[j] |= kJHuge;
           pl->any_huge = true;

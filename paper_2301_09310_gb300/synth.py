@@ -128,6 +128,20 @@ WORKLOADS = {
 }
 
 
+# Equal-length reads of the paper's kernel comparison (Sec. V-B): 5,000 pairs per
+# call at each length L in 64..4096 from a wgsim-like simulator.  Here: target =
+# a reference window of L bases, query = a copy with 2% substitutions (base
+# errors) and 0.1% indels, both L long; the whole table is the band (w = L) and
+# z-drop is off, so every pair extends over all L x L cells.
+X2_LENGTHS = (64, 128, 256, 512, 1024, 2048, 4096)
+
+
+def x2_workload(L: int, n_pairs: int = 5000) -> Workload:
+    return Workload(f"x2_{L}", n_pairs, 100 + L.bit_length(), 0, qlen_fixed=L, tlen_extra=0,
+                    p_sub=0.02, p_ins=0.0005, p_del=0.0005, h0_lo=20, h0_hi=40,
+                    scoring=ScoringParams(w=L, zdrop=0))
+
+
 def lib_path() -> str:
     return os.path.join(_HERE, "_build", f"libxt_synth.{platform.machine()}.so")
 

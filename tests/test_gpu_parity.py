@@ -181,3 +181,26 @@ def test_graph_replay_matches_direct(ctx):
             assert_same(run_gpu(ctx, b, wl.scoring), w, f"graph replay {rep}")
     for b in batches[2:4]:
         assert_same(run_gpu(ctx, b, wl.scoring), run_oracle(b, wl.scoring), "graph vs oracle")
+
+
+@pytest.mark.parametrize("L", [64, 300, 1100])
+def test_equal_length_unbanded(ctx, L):
+    # the paper's kernel comparison regime: qlen = tlen, band = whole table,
+    # z-drop off; built-in schedule and explicit one-lane / group schedules
+    import paper_2301_09310_gb300 as xt
+    wl = synth.x2_workload(L)
+    b = synth.generate(wl, n=40 if L < 1000 else 12)
+    want = run_oracle(b, wl.scoring)
+    assert np.all(want[1] == (want[1] > 0) * L * L)   # full tables while alive
+    assert_same(run_gpu(ctx, b, wl.scoring), want, f"x2 {L} built-in")
+    j = int(np.ceil(np.log2(L + 2)))
+    other = xt.Context(0)
+    try:
+        for P, R in ((1, 8), (8, 8), (32, 4)):
+            try:
+                other.set_bucket_schedule(wl.scoring.w, j, P, R)
+            except xt.XtError:
+                continue
+            assert_same(run_gpu(other, b, wl.scoring), want, f"x2 {L} P{P}R{R}")
+    finally:
+        other.close()
