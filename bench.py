@@ -520,10 +520,6 @@ def serve_leg(args, local, stream):
     batched path's peak pairs/s on the same mix.  Latency of a request is from
     its scheduled arrival to its results in host memory (xt_serve_times
     stamps, CLOCK_MONOTONIC, the clock of time.monotonic_ns)."""
-    import ctypes
-    import queue
-    import threading
-
     import torch
     import paper_2301_09310_gb300 as xt
     from paper_2301_09310_gb300 import synth
@@ -531,8 +527,19 @@ def serve_leg(args, local, stream):
     wl = synth.WORKLOADS["c5_stream"]
     b = synth.generate(wl, n=args.serve_pairs)
     dev = torch.device("cuda", local)
-    # peak of the batched path on this mix: device-resident, one call per step
+    # schedules tuned for this mix, for large and for small calls; every slot
+    # context of the server loads the table
+    import tempfile
+    table = os.path.join(tempfile.mkdtemp(prefix="xt_tune_"), "tuning.json")
+    j_max = max(5, int(np.ceil(np.log2(int(b.q_len.max()) + 2))))
     ctx = xt.Context(local)
+    t0 = time.perf_counter()
+    ctx.autotune(wl.scoring, j_max=j_max, table_path=table)
+    tune_s = time.perf_counter() - t0
+    sched = {f"j{j}": "P{}R{}/P{}R{}".format(*ctx.bucket_schedule(wl.scoring.w, j, xt.XT_BATCH_LARGE),
+                                            *ctx.bucket_schedule(wl.scoring.w, j, xt.XT_BATCH_SMALL))
+             for j in range(5, j_max + 1)}
+    # peak of the batched path on this mix: device-resident, one call per step
     d = [torch.from_numpy(a).to(dev) for a in
          (b.q_seq, b.q_off, b.q_len, b.t_seq, b.t_off, b.t_len, b.h0)]
     out_d = torch.empty((b.n, 7), dtype=torch.int32, device=dev)
@@ -552,10 +559,34 @@ def serve_leg(args, local, stream):
     total_cells = int(ref_cells.sum())
     ctx.close()
     del d, out_d, cells_d
-    lib = xt.load_library()
-    sc = xt._scoring(wl.scoring)
     old_switch = sys.getswitchinterval()
     sys.setswitchinterval(2e-4)
+    tuned = serve_levels(args, local, b, wl, peak_pairs, ref_out, ref_cells, total_cells, table)
+    builtin = serve_levels(args, local, b, wl, peak_pairs, ref_out, ref_cells, total_cells, None)
+    sys.setswitchinterval(old_switch)
+    return {"workload": f"c5_stream: {args.serve_pairs:,} pairs, qlen lognormal median 120 "
+                        "sigma 1 clipped [1,2000], tlen = qlen + 200; requests U[1,4096] "
+                        "pairs, Poisson arrivals",
+            "api": f"xt_serve_submit/xt_serve_wait (host buffers; {args.serve_slots} slots, "
+                   f"gather threads {args.serve_gather_threads or 'default'})",
+            "latency": "scheduled arrival -> results in host memory",
+            "tuning": {"seconds": round(tune_s, 2), "schedule_large/small": sched},
+            "peak_batched_pairs_per_s": round(peak_pairs, 1),
+            "peak_batched_gcups": round(total_cells / (peak_ms / 1e3) / 1e9, 3),
+            "levels": tuned, "levels_builtin_schedule": builtin}
+
+
+def serve_levels(args, local, b, wl, peak_pairs, ref_out, ref_cells, total_cells, table):
+    """Run the request stream at 25/50/90% of peak_pairs through a server."""
+    import ctypes
+    import queue
+    import threading
+
+    import paper_2301_09310_gb300 as xt
+    from paper_2301_09310_gb300 import synth
+
+    lib = xt.load_library()
+    sc = xt._scoring(wl.scoring)
     levels = []
     for frac in (0.25, 0.5, 0.9):
         rs = synth.request_stream(b, frac * peak_pairs, seed=5)
@@ -573,8 +604,9 @@ def serve_leg(args, local, stream):
                           ctypes.c_void_p(h0.ctypes.data), int(rs.size[r]), ctypes.byref(sc),
                           ctypes.c_void_p(out.ctypes.data + 28 * a),
                           ctypes.c_void_p(cells.ctypes.data + 8 * a)))
-        srv = xt.xt_serve_create(local, xt.xt_serve_config(args.serve_slots, 0, 0, 0, 0,
-                                                           args.serve_gather_threads))
+        srv = xt.xt_serve_create(local, xt.xt_serve_config(
+            args.serve_slots, 0, 0, 0, 0, args.serve_gather_threads,
+            table.encode() if table else None))
         tickets = queue.Queue()
         stamps = np.zeros((nreq, 4), np.int64)   # arrival, submit, launch, done
         bpairs = np.zeros(nreq, np.int64)
@@ -637,16 +669,7 @@ def serve_leg(args, local, stream):
             "equal_to_batched": bool(np.array_equal(out, ref_out)
                                      and np.array_equal(cells, ref_cells)),
         })
-    sys.setswitchinterval(old_switch)
-    return {"workload": f"c5_stream: {args.serve_pairs:,} pairs, qlen lognormal median 120 "
-                        "sigma 1 clipped [1,2000], tlen = qlen + 200; requests U[1,4096] "
-                        "pairs, Poisson arrivals",
-            "api": f"xt_serve_submit/xt_serve_wait (host buffers; {args.serve_slots} slots, "
-                   f"gather threads {args.serve_gather_threads or 'default'})",
-            "latency": "scheduled arrival -> results in host memory",
-            "peak_batched_pairs_per_s": round(peak_pairs, 1),
-            "peak_batched_gcups": round(total_cells / (peak_ms / 1e3) / 1e9, 3),
-            "levels": levels}
+    return levels
 
 
 def _max_op():

@@ -211,14 +211,27 @@ xt_status xt_ctx_set_streams(xt_ctx* ctx, int branches);
  * per pair and R rows per lane: P = 1 is the one-lane engine (one thread per
  * pair, R = 4, 8 or 16; packed 16-bit where exact), P = 2..32 the group
  * engine (P lanes of a warp per pair, R = 4 or 8, or 16 with P <= 4).
- * Schedules are kept per band w: a call uses the schedules set for its own
- * scoring's w and the built-in rule for buckets without one.  P = 0 removes
- * a bucket's schedule.  XT_EINVAL if (P, R) does not exist or its band ring
- * does not fit on this device.  Results never depend on the schedule.
+ * Schedules are kept per band w and per batch class: XT_BATCH_SMALL
+ * schedules apply to calls of at most XT_SMALL_BATCH pairs (there a pair's
+ * latency on its engine bounds the call), XT_BATCH_LARGE ones to larger
+ * calls, and to small calls whose bucket has no small-batch schedule.  A
+ * call uses the schedules set for its own scoring's w and the built-in rule
+ * for buckets without one.  P = 0 removes a bucket's schedule.  XT_EINVAL if
+ * (P, R) does not exist or its band ring does not fit on this device.
+ * Results never depend on the schedule.  xt_ctx_set_bucket_schedule sets
+ * both classes.
  */
+#define XT_BATCH_LARGE 0
+#define XT_BATCH_SMALL 1
+#define XT_SMALL_BATCH 32768
 xt_status xt_ctx_set_bucket_schedule(xt_ctx* ctx, int w, int j, int P, int R);
-/* The schedule set for (w, j): *P = 0 when the built-in rule applies. */
+xt_status xt_ctx_set_bucket_schedule_for(xt_ctx* ctx, int w, int j, int batch_class, int P,
+                                         int R);
+/* The schedule set for (w, j) (large batches, or the given class): *P = 0
+ * when the built-in rule applies. */
 xt_status xt_ctx_get_bucket_schedule(xt_ctx* ctx, int w, int j, int* P, int* R);
+xt_status xt_ctx_get_bucket_schedule_for(xt_ctx* ctx, int w, int j, int batch_class, int* P,
+                                         int* R);
 
 /*
  * Autotuner.  For every bucket j = 5..j_max, times each available (P, R) on
@@ -323,6 +336,8 @@ typedef struct {
   size_t mem_budget_bytes;  /* device memory of the whole server (0: no cap) */
   int32_t gather_threads;   /* host threads staging a batch, 1..16, the server
                                thread included (0: a quarter of the cores, <= 8) */
+  const char* tuning_path;  /* a table written by xt_autotune, loaded into every
+                               slot's context (NULL: built-in schedules) */
 } xt_serve_config;
 
 /* Latency stamps of one request, ns on CLOCK_MONOTONIC (see xt_now_ns). */

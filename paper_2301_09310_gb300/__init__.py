@@ -27,7 +27,8 @@ EXPORTED = ("xt_ctx_create", "xt_ctx_destroy", "xt_ctx_sync", "xt_extend_batch",
             "xt_serve_create", "xt_serve_submit", "xt_serve_poll", "xt_serve_wait",
             "xt_serve_pause", "xt_serve_get_stats", "xt_serve_destroy", "xt_ctx_set_streams",
             "xt_ctx_set_bucket_schedule", "xt_ctx_get_bucket_schedule", "xt_autotune",
-            "xt_ctx_load_tuning")
+            "xt_ctx_load_tuning", "xt_ctx_set_bucket_schedule_for",
+            "xt_ctx_get_bucket_schedule_for")
 XT_STATIC_MAX_PAIRS = 1 << 20
 
 
@@ -45,7 +46,8 @@ class xt_stats(ctypes.Structure):
 class xt_serve_config(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("max_batch_pairs", ctypes.c_int32),
                 ("max_batch_bytes", ctypes.c_int64), ("max_queued_bytes", ctypes.c_int64),
-                ("mem_budget_bytes", ctypes.c_size_t), ("gather_threads", ctypes.c_int32)]
+                ("mem_budget_bytes", ctypes.c_size_t), ("gather_threads", ctypes.c_int32),
+                ("tuning_path", ctypes.c_char_p)]
 
 
 class xt_serve_times(ctypes.Structure):
@@ -111,6 +113,13 @@ def load_library(path: str | None = None):
     lib.xt_ctx_get_bucket_schedule.argtypes = [P, ctypes.c_int, ctypes.c_int,
                                                ctypes.POINTER(ctypes.c_int),
                                                ctypes.POINTER(ctypes.c_int)]
+    lib.xt_ctx_set_bucket_schedule_for.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                   ctypes.c_int, ctypes.c_int]
+    lib.xt_ctx_get_bucket_schedule_for.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                   ctypes.POINTER(ctypes.c_int),
+                                                   ctypes.POINTER(ctypes.c_int)]
+    lib.xt_ctx_set_bucket_schedule_for.restype = ctypes.c_int
+    lib.xt_ctx_get_bucket_schedule_for.restype = ctypes.c_int
     lib.xt_autotune.argtypes = [P, ctypes.POINTER(xt_scoring), ctypes.c_int, ctypes.c_double,
                                 ctypes.c_char_p]
     lib.xt_ctx_load_tuning.argtypes = [P, ctypes.c_char_p]
@@ -140,7 +149,8 @@ def load_library(path: str | None = None):
     for fn in ("xt_serve_create", "xt_serve_submit", "xt_serve_poll", "xt_serve_wait",
                "xt_serve_pause", "xt_serve_get_stats", "xt_serve_destroy", "xt_ctx_set_streams",
             "xt_ctx_set_bucket_schedule", "xt_ctx_get_bucket_schedule", "xt_autotune",
-            "xt_ctx_load_tuning"):
+            "xt_ctx_load_tuning", "xt_ctx_set_bucket_schedule_for",
+            "xt_ctx_get_bucket_schedule_for"):
         getattr(lib, fn).restype = ctypes.c_int
     _LIB = lib
     return lib
@@ -180,6 +190,24 @@ def xt_ctx_get_bucket_schedule(ctx: int, w: int, j: int) -> tuple[int, int, int]
     P, R = ctypes.c_int(0), ctypes.c_int(0)
     s = load_library().xt_ctx_get_bucket_schedule(ctypes.c_void_p(ctx), int(w), int(j),
                                                   ctypes.byref(P), ctypes.byref(R))
+    return s, P.value, R.value
+
+
+XT_BATCH_LARGE, XT_BATCH_SMALL, XT_SMALL_BATCH = 0, 1, 32768
+
+
+def xt_ctx_set_bucket_schedule_for(ctx: int, w: int, j: int, batch_class: int, P: int,
+                                   R: int) -> int:
+    return load_library().xt_ctx_set_bucket_schedule_for(ctypes.c_void_p(ctx), int(w), int(j),
+                                                         int(batch_class), int(P), int(R))
+
+
+def xt_ctx_get_bucket_schedule_for(ctx: int, w: int, j: int,
+                                   batch_class: int) -> tuple[int, int, int]:
+    P, R = ctypes.c_int(0), ctypes.c_int(0)
+    s = load_library().xt_ctx_get_bucket_schedule_for(ctypes.c_void_p(ctx), int(w), int(j),
+                                                      int(batch_class), ctypes.byref(P),
+                                                      ctypes.byref(R))
     return s, P.value, R.value
 
 
@@ -375,10 +403,14 @@ class Context:
         self._check(xt_ctx_set_bucket_schedule(self.handle, w, j, P, R),
                     "xt_ctx_set_bucket_schedule")
 
-    def bucket_schedule(self, w: int, j: int) -> tuple[int, int]:
-        s, P, R = xt_ctx_get_bucket_schedule(self.handle, w, j)
-        self._check(s, "xt_ctx_get_bucket_schedule")
+    def bucket_schedule(self, w: int, j: int, batch_class: int = XT_BATCH_LARGE) -> tuple[int, int]:
+        s, P, R = xt_ctx_get_bucket_schedule_for(self.handle, w, j, batch_class)
+        self._check(s, "xt_ctx_get_bucket_schedule_for")
         return P, R
+
+    def set_bucket_schedule_for(self, w: int, j: int, batch_class: int, P: int, R: int = 8):
+        self._check(xt_ctx_set_bucket_schedule_for(self.handle, w, j, batch_class, P, R),
+                    "xt_ctx_set_bucket_schedule_for")
 
     def autotune(self, scoring, j_max: int = 14, cells_per_trial: float = 0.0,
                  table_path: str | None = None):
@@ -480,9 +512,10 @@ class Server:
 
     def __init__(self, device: int = 0, slots: int = 0, max_batch_pairs: int = 0,
                  max_batch_bytes: int = 0, max_queued_bytes: int = 0, mem_budget_bytes: int = 0,
-                 gather_threads: int = 0):
+                 gather_threads: int = 0, tuning_path: str | None = None):
         cfg = xt_serve_config(slots, max_batch_pairs, max_batch_bytes, max_queued_bytes,
-                              mem_budget_bytes, gather_threads)
+                              mem_budget_bytes, gather_threads,
+                              tuning_path.encode() if tuning_path else None)
         self.handle = xt_serve_create(device, cfg)
         self._live = {}
 

@@ -142,11 +142,15 @@ int64_t next_pow2(int64_t x) { return (int64_t)1 << log2_ceil(x); }
 // Schedule of bucket j (queries of qlen + 2 <= 2^j): the fewest lanes per pair
 // whose shared-memory ring fits 32 KB per CTA.  The ring needs
 // min(qlen, P*R + 2w) + 2 entries.
-// The tuned schedule of bucket j for band w, or nullptr (built-in rule).
+// The tuned schedule of bucket j for band w and the size class of the call
+// being planned, or nullptr (built-in rule).
 const BucketSched* tuned(const xt_ctx* ctx, int w, int j) {
   if (ctx->forced_P) return nullptr;
-  for (const auto& t : ctx->tuning)
-    if (t.w == w && t.b[j].P > 0) return &t.b[j];
+  for (const auto& t : ctx->tuning) {
+    if (t.w != w) continue;
+    if (ctx->plan_small && t.small[j].P > 0) return &t.small[j];
+    if (t.b[j].P > 0) return &t.b[j];
+  }
   return nullptr;
 }
 
@@ -205,8 +209,9 @@ void add_huge_launch(xt_ctx* ctx, const Score& sc, Plan* pl) {
   if (grid > 2 * ctx->num_sms) grid = 2 * ctx->num_sms;
   if (grid < 1) grid = 1;
   Launch& L = pl->launch[pl->n_launch++];
-  L.cls = CLS_HUGE; L.j_lo = 0; L.j_hi = kJMax; L.P = 32; L.R = 8; L.rs_log2 = 0;
-  L.global_ring = true; L.slab = pl->slab; L.grid = (int)grid;
+  L = Launch();
+  L.cls = CLS_HUGE; L.j_lo = 0; L.j_hi = kJMax; L.lane = false; L.P = 32; L.R = 8;
+  L.rs_log2 = 0; L.global_ring = true; L.slab = pl->slab; L.grid = (int)grid; L.mparam = 0;
 }
 
 constexpr int kLaneJMax = 9;           // one-lane engine for queries up to 2^9 - 2 bases
@@ -424,6 +429,7 @@ xt_status run(xt_ctx* ctx, bool plain, const uint8_t* q_seq, int64_t q_bytes, co
   Plan pl;
   int plain_rs = 0;
   ctx->match = scr->match;
+  ctx->plan_small = n_cap <= kSmallBatchMax;
   if (plain) plan_plain(ctx, sc, &pl, &plain_rs);
   else plan_batched(ctx, sc, &pl);
   const size_t want = pool_bytes(pl);
@@ -650,7 +656,15 @@ xt_status xt_ctx_set_graphs(xt_ctx* ctx, int enable) {
 }
 
 xt_status xt_ctx_set_bucket_schedule(xt_ctx* ctx, int w, int j, int P, int R) {
+  xt_status s = xt_ctx_set_bucket_schedule_for(ctx, w, j, XT_BATCH_LARGE, P, R);
+  if (s == XT_OK) s = xt_ctx_set_bucket_schedule_for(ctx, w, j, XT_BATCH_SMALL, P, R);
+  return s;
+}
+
+xt_status xt_ctx_set_bucket_schedule_for(xt_ctx* ctx, int w, int j, int batch_class, int P,
+                                         int R) {
   if (!ctx || w < 0 || j < kJMin || j > kJMax) return XT_EINVAL;
+  if (batch_class != XT_BATCH_LARGE && batch_class != XT_BATCH_SMALL) return XT_EINVAL;
   const int wc = w > 2 * XT_MAX_LEN ? 2 * XT_MAX_LEN : w;  // the band the plan sees
   if (P != 0 && !bucket_sched_ok(ctx, wc, j, P, R))
     return fail(ctx, XT_EINVAL, "schedule not available for this bucket and band");
@@ -663,22 +677,30 @@ xt_status xt_ctx_set_bucket_schedule(xt_ctx* ctx, int w, int j, int P, int R) {
     e = &ctx->tuning.back();
     e->w = wc;
   }
-  e->b[j].P = P;
-  e->b[j].R = P ? R : 0;
+  BucketSched& b = batch_class == XT_BATCH_SMALL ? e->small[j] : e->b[j];
+  b.P = P;
+  b.R = P ? R : 0;
   drop_graphs(ctx);
   return XT_OK;
 }
 
 xt_status xt_ctx_get_bucket_schedule(xt_ctx* ctx, int w, int j, int* P, int* R) {
+  return xt_ctx_get_bucket_schedule_for(ctx, w, j, XT_BATCH_LARGE, P, R);
+}
+
+xt_status xt_ctx_get_bucket_schedule_for(xt_ctx* ctx, int w, int j, int batch_class, int* P,
+                                         int* R) {
   if (!ctx || !P || !R || w < 0 || j < kJMin || j > kJMax) return XT_EINVAL;
+  if (batch_class != XT_BATCH_LARGE && batch_class != XT_BATCH_SMALL) return XT_EINVAL;
   const int wc = w > 2 * XT_MAX_LEN ? 2 * XT_MAX_LEN : w;
   std::lock_guard<std::mutex> lk(ctx->mu);
   *P = 0;
   *R = 0;
   for (auto& t : ctx->tuning)
     if (t.w == wc) {
-      *P = t.b[j].P;
-      *R = t.b[j].R;
+      const BucketSched& b = batch_class == XT_BATCH_SMALL ? t.small[j] : t.b[j];
+      *P = b.P;
+      *R = b.R;
     }
   return XT_OK;
 }

@@ -35,10 +35,15 @@ constexpr int kMaxBranches = 8;  // streams the DP launches of one call fork ont
 struct BucketSched {
   int P = 0, R = 0;
 };
-// The schedules of every bucket for calls whose band is w.
+// The schedules of every bucket for calls whose band is w: one set for large
+// calls (tuned at saturation) and one for calls of at most kSmallBatchMax
+// pairs (tuned on small trials: there a pair's latency on its engine, not
+// the engine's throughput, decides the call's time).
+constexpr int32_t kSmallBatchMax = XT_SMALL_BATCH;
 struct TuneEntry {
   int w = 0;
   BucketSched b[kNumJ];
+  BucketSched small[kNumJ];
 };
 
 // Whether (P, R) is an instantiated schedule whose ring fits for bucket j
@@ -87,6 +92,7 @@ struct xt_ctx {
   int forced_P = 0;              // schedule override (0: per-bucket table)
   int forced_R = 0;
   std::vector<xt::TuneEntry> tuning;  // per-band bucket schedules (xt_autotune)
+  bool plan_small = false;       // the call being planned has at most kSmallBatchMax pairs
   std::mutex mu;
   std::string last_error;
 };

@@ -40,16 +40,18 @@ struct Work {
 constexpr int kLaneThreads = 128;        // threads per CTA of the one-lane kernels
 constexpr int kLaneStageJMax = 9;        // one-lane kernels stage queries up to 2^9 - 2 bases
 
-// One persistent launch: pairs of class cls, buckets [j_lo, j_hi].
+// One persistent launch: pairs of class cls, buckets [j_lo, j_hi].  Every
+// field has a default, so a launch built field by field never carries stack
+// contents into the dispatch.
 struct Launch {
-  int cls, j_lo, j_hi;
-  bool lane;           // one-lane engine (k_lane) instead of the group engine (k_queue)
-  int P, R;            // lanes per pair, rows per lane-strip (per half when packed)
-  int rs_log2;         // ring entries per group = 1 << rs_log2
-  bool global_ring;    // ring in a global slab per group instead of shared memory
-  int64_t slab;        // entries per global slab (power of two)
-  int grid;            // CTAs
-  int mparam;          // one-lane engine: match + 1 (32-bit) or shift k (packed)
+  int cls = 0, j_lo = 0, j_hi = 0;
+  bool lane = false;         // one-lane engine (k_lane) instead of the group engine (k_queue)
+  int P = 1, R = 8;          // lanes per pair, rows per lane-strip (per half when packed)
+  int rs_log2 = 0;           // ring entries per group = 1 << rs_log2
+  bool global_ring = false;  // ring in a global slab per group instead of shared memory
+  int64_t slab = 0;          // entries per global slab (power of two)
+  int grid = 0;              // CTAs
+  int mparam = 0;            // one-lane engine: match + 1 (32-bit) or shift k (packed)
 };
 
 // Host-side launchers (defined in xt_kernels.cu); all enqueue on `stream`.

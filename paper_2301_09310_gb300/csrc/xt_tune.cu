@@ -178,6 +178,8 @@ struct Entry {
   struct B {
     int j, P, R;
     double gcups;
+    int Ps, Rs;  // small-batch schedule (0: none)
+    double gcups_s;
   };
   std::vector<B> buckets;
 };
@@ -200,7 +202,11 @@ bool entry_from_json(const Json& e, Entry* out) {
     const Json *j = b.get("j"), *P = b.get("P"), *R = b.get("R"), *g = b.get("gcups");
     if (!j || !P || !R || j->kind != Json::NUM || P->kind != Json::NUM || R->kind != Json::NUM)
       return false;
-    out->buckets.push_back({(int)j->num, (int)P->num, (int)R->num, g ? g->num : 0.0});
+    const Json *Ps = b.get("Ps"), *Rs = b.get("Rs"), *gs = b.get("gcups_s");
+    const bool small = Ps && Rs && Ps->kind == Json::NUM && Rs->kind == Json::NUM;
+    out->buckets.push_back({(int)j->num, (int)P->num, (int)R->num, g ? g->num : 0.0,
+                            small ? (int)Ps->num : 0, small ? (int)Rs->num : 0,
+                            gs ? gs->num : 0.0});
   }
   return true;
 }
@@ -214,8 +220,10 @@ std::string entry_to_json(const Entry& e) {
   s += buf;
   for (size_t k = 0; k < e.buckets.size(); ++k) {
     const auto& b = e.buckets[k];
-    std::snprintf(buf, sizeof(buf), "%s\n       {\"j\": %d, \"P\": %d, \"R\": %d, \"gcups\": %.3f}",
-                  k ? "," : "", b.j, b.P, b.R, b.gcups);
+    std::snprintf(buf, sizeof(buf),
+                  "%s\n       {\"j\": %d, \"P\": %d, \"R\": %d, \"gcups\": %.3f, "
+                  "\"Ps\": %d, \"Rs\": %d, \"gcups_s\": %.3f}",
+                  k ? "," : "", b.j, b.P, b.R, b.gcups, b.Ps, b.Rs, b.gcups_s);
     s += buf;
   }
   return s + "]}";
@@ -351,7 +359,7 @@ std::string device_name(int dev) {
   return p.name;
 }
 
-void set_sched(xt_ctx* ctx, int w, int j, BucketSched s) {
+void set_sched(xt_ctx* ctx, int w, int j, BucketSched s, bool small) {
   TuneEntry* e = nullptr;
   for (auto& t : ctx->tuning)
     if (t.w == w) e = &t;
@@ -360,8 +368,91 @@ void set_sched(xt_ctx* ctx, int w, int j, BucketSched s) {
     e = &ctx->tuning.back();
     e->w = w;
   }
-  e->b[j] = s;
+  (small ? e->small[j] : e->b[j]) = s;
   drop_graphs(ctx);
+}
+
+constexpr int kSmallTrialPairs = 2048;
+
+struct Trial {
+  BucketSched best{};
+  double gcups = -1;
+};
+
+// Time every candidate schedule of bucket j on n synthetic pairs; every
+// candidate must reproduce the first one's results.
+xt_status tune_bucket(xt_ctx* ctx, const xt_scoring* sc, int w, int j, int n,
+                      const std::vector<BucketSched>& cand, bool small_only, int reps, Trial* tr,
+                      std::string* why) {
+  HostPairs hp;
+  make_pairs(j, w, n, 0x5EED0000u + (uint64_t)j + (small_only ? 77u : 0u), &hp);
+  DevPairs d;
+  if (upload(hp, &d) != cudaSuccess) {
+    cudaGetLastError();
+    *why = "tuning buffers";
+    return XT_ENOMEM;
+  }
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    if (st) cudaStreamDestroy(st);
+    if (e0) cudaEventDestroy(e0);
+    *why = "tuning stream";
+    return XT_ECUDA;
+  }
+  std::vector<xt_result> first_out(n), out(n);
+  std::vector<int64_t> first_cells(n), cells(n);
+  xt_status status = XT_OK;
+  for (size_t c = 0; c < cand.size() && status == XT_OK; ++c) {
+    {
+      std::lock_guard<std::mutex> lk(ctx->mu);
+      set_sched(ctx, w, j, cand[c], true);
+      if (!small_only) set_sched(ctx, w, j, cand[c], false);
+    }
+    auto call = [&] {
+      return xt_extend_batch(ctx, d.q, (int64_t)hp.q.size(), d.qo, d.ql, d.t,
+                             (int64_t)hp.t.size(), d.to, d.tl, d.h0, n, sc, d.out, d.cells, st);
+    };
+    xt_status s = call();
+    if (s != XT_OK) { status = s; *why = "tuning call"; break; }
+    cudaError_t e = cudaMemcpyAsync(out.data(), d.out, sizeof(xt_result) * n,
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(cells.data(), d.cells, 8 * (size_t)n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { status = XT_ECUDA; *why = cudaGetErrorString(e); break; }
+    if (c == 0) {
+      first_out = out;
+      first_cells = cells;
+    } else if (std::memcmp(out.data(), first_out.data(), sizeof(xt_result) * n) != 0 ||
+               cells != first_cells) {
+      status = XT_ECUDA;
+      *why = "schedules disagree on bucket " + std::to_string(j);
+      break;
+    }
+    int64_t total = 0;
+    for (int64_t v : cells) total += v;
+    e = cudaEventRecord(e0, st);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+      if (call() != XT_OK) e = cudaErrorUnknown;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) { status = XT_ECUDA; *why = cudaGetErrorString(e); break; }
+    const double gcups = (double)total / (ms / reps * 1e-3) / 1e9;
+    if (gcups > tr->gcups) {
+      tr->gcups = gcups;
+      tr->best = cand[c];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(st);
+  return status;
 }
 
 }  // namespace
@@ -383,15 +474,6 @@ xt_status xt_autotune(xt_ctx* ctx, const xt_scoring* sc, int j_max, double cells
     }
   }
   if (cudaSetDevice(ctx->device) != cudaSuccess) return XT_ECUDA;
-  cudaStream_t st = nullptr;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
-    cudaGetLastError();
-    if (st) cudaStreamDestroy(st);
-    if (e0) cudaEventDestroy(e0);
-    return XT_ECUDA;
-  }
   Entry entry;
   entry.device = device_name(ctx->device);
   entry.sms = ctx->num_sms;
@@ -411,85 +493,40 @@ xt_status xt_autotune(xt_ctx* ctx, const xt_scoring* sc, int j_max, double cells
       cand = candidates(ctx, w, j);
     }
     if (cand.empty()) continue;
-    // a trial fills the GPU: four pairs per one-lane thread slot (so every
-    // schedule is timed at saturation, as in a large batch), unless that
-    // exceeds the cells budget
+    // large calls: a trial fills the GPU, four pairs per one-lane thread slot
+    // (every schedule timed at saturation), unless that exceeds the cells
+    // budget; the candidate is set for both classes, since a capped trial
+    // may itself be a small call
     const double qmid = j == kJMin ? 16.0 : 0.75 * (1 << j);
     const double width = std::min<double>(2.0 * w + 1, qmid + std::min<double>(2.0 * w, 2.0 * qmid));
     const double n_fill = 4.0 * ctx->num_sms * 4 * kLaneThreads;
     const int n = (int)std::max(1024.0, std::min<double>({(double)(1 << 20), n_fill,
                                                           cells_per_trial / (qmid * width)}));
-    HostPairs hp;
-    make_pairs(j, w, n, 0x5EED0000u + (uint64_t)j, &hp);
-    DevPairs d;
-    if (upload(hp, &d) != cudaSuccess) {
-      status = XT_ENOMEM;
-      why = "tuning buffers";
-      break;
-    }
-    std::vector<xt_result> first_out(n), out(n);
-    std::vector<int64_t> first_cells(n), cells(n);
-    double best_gcups = -1;
-    BucketSched best{};
-    for (size_t c = 0; c < cand.size() && status == XT_OK; ++c) {
-      {
-        std::lock_guard<std::mutex> lk(ctx->mu);
-        set_sched(ctx, w, j, cand[c]);
-      }
-      auto call = [&] {
-        return xt_extend_batch(ctx, d.q, (int64_t)hp.q.size(), d.qo, d.ql, d.t,
-                               (int64_t)hp.t.size(), d.to, d.tl, d.h0, n, sc, d.out, d.cells, st);
-      };
-      xt_status s = call();
-      if (s != XT_OK) { status = s; why = "tuning call"; break; }
-      cudaError_t e = cudaMemcpyAsync(out.data(), d.out, sizeof(xt_result) * n,
-                                      cudaMemcpyDeviceToHost, st);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(cells.data(), d.cells, 8 * (size_t)n, cudaMemcpyDeviceToHost, st);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-      if (e != cudaSuccess) { status = XT_ECUDA; why = cudaGetErrorString(e); break; }
-      if (c == 0) {
-        first_out = out;
-        first_cells = cells;
-      } else if (std::memcmp(out.data(), first_out.data(), sizeof(xt_result) * n) != 0 ||
-                 cells != first_cells) {
-        status = XT_ECUDA;
-        why = "schedules disagree on bucket " + std::to_string(j);
-        break;
-      }
-      int64_t total = 0;
-      for (int64_t v : cells) total += v;
-      const int reps = 3;
-      e = cudaEventRecord(e0, st);
-      for (int r = 0; r < reps && e == cudaSuccess; ++r) {
-        if (call() != XT_OK) e = cudaErrorUnknown;
-      }
-      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
-      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-      float ms = 0;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-      if (e != cudaSuccess) { status = XT_ECUDA; why = cudaGetErrorString(e); break; }
-      const double gcups = (double)total / (ms / reps * 1e-3) / 1e9;
-      if (gcups > best_gcups) {
-        best_gcups = gcups;
-        best = cand[c];
-      }
-    }
+    Trial big;
+    status = tune_bucket(ctx, sc, w, j, n, cand, /*small_only=*/false, 3, &big, &why);
     if (status != XT_OK) break;
     {
       std::lock_guard<std::mutex> lk(ctx->mu);
-      set_sched(ctx, w, j, best);
+      set_sched(ctx, w, j, big.best, false);
+      set_sched(ctx, w, j, big.best, true);
     }
-    entry.buckets.push_back({j, best.P, best.R, best_gcups});
+    // small calls: a bucket's share of a call of a few thousand pairs
+    Trial little;
+    status = tune_bucket(ctx, sc, w, j, kSmallTrialPairs, cand, /*small_only=*/true, 10, &little,
+                         &why);
+    if (status != XT_OK) break;
+    {
+      std::lock_guard<std::mutex> lk(ctx->mu);
+      set_sched(ctx, w, j, little.best, true);
+    }
+    entry.buckets.push_back({j, big.best.P, big.best.R, big.gcups, little.best.P, little.best.R,
+                             little.gcups});
   }
   {
     std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->graphs = graphs;
     if (status != XT_OK) ctx->last_error = "xt_autotune: " + why;
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  cudaStreamDestroy(st);
   if (status != XT_OK) return status;
   if (table_path) {
     std::vector<Entry> all = read_entries(table_path);
@@ -518,9 +555,12 @@ xt_status xt_ctx_load_tuning(xt_ctx* ctx, const char* table_path) {
   std::lock_guard<std::mutex> lk(ctx->mu);
   for (const Entry& e : read_entries(table_path)) {
     if (e.device != dev || e.sms != ctx->num_sms || e.w < 0) continue;
-    for (const auto& b : e.buckets)
-      if (b.j >= kJMin && b.j <= kJMax && bucket_sched_ok(ctx, e.w, b.j, b.P, b.R))
-        set_sched(ctx, e.w, b.j, {b.P, b.R});
+    for (const auto& b : e.buckets) {
+      if (b.j < kJMin || b.j > kJMax) continue;
+      if (bucket_sched_ok(ctx, e.w, b.j, b.P, b.R)) set_sched(ctx, e.w, b.j, {b.P, b.R}, false);
+      if (b.Ps > 0 && bucket_sched_ok(ctx, e.w, b.j, b.Ps, b.Rs))
+        set_sched(ctx, e.w, b.j, {b.Ps, b.Rs}, true);
+    }
   }
   return XT_OK;
 }

@@ -93,11 +93,27 @@ def test_huge_band_global_ring(ctx):
         qs.append(q)
         ts.append(np.concatenate([t, rng.integers(0, 4, 500)]))
         hs.append(30)
+    # 2,200-base queries with w = 1000: a shared ring would leave one CTA per
+    # SM, so these take the global slabs too
+    for k in range(3):
+        q = rng.integers(0, 4, 2200 + 100 * k)
+        t = q.copy()
+        mut = rng.random(t.size) < 0.03
+        t[mut] = rng.integers(0, 4, int(mut.sum()))
+        qs.append(q)
+        ts.append(np.concatenate([t, rng.integers(0, 4, 500)]))
+        hs.append(30)
     b = batch_from_lists(qs, ts, hs)
-    sc = ScoringParams(w=6000, zdrop=300)
-    want = run_oracle(b, sc)
-    assert_same(run_gpu(ctx, b, sc), want, "huge batched")
-    assert_same(run_gpu(ctx, b, sc, plain=True), want, "huge plain")
+    import paper_2301_09310_gb300 as xt
+    for sc in (ScoringParams(w=6000, zdrop=300), ScoringParams(w=1000, zdrop=300)):
+        want = run_oracle(b, sc)
+        assert_same(run_gpu(ctx, b, sc), want, f"huge batched w={sc.w}")
+        assert_same(run_gpu(ctx, b, sc, plain=True), want, f"huge plain w={sc.w}")
+        fresh = xt.Context(0)      # a new context's first plan, on a fresh stack
+        try:
+            assert_same(run_gpu(fresh, b, sc), want, f"huge fresh context w={sc.w}")
+        finally:
+            fresh.close()
 
 
 def test_wide_scores(ctx):

@@ -176,3 +176,25 @@ def test_concurrent_submitters(xt):
         a, n = int(rs.start[k]), int(rs.size[k])
         out, cells, _ = results[k]
         check(out, cells, (want[0][a:a + n], want[1][a:a + n]), f"request {k}")
+
+
+def test_server_with_tuning_table(xt, tmp_path):
+    path = str(tmp_path / "tuning.json")
+    ctx = xt.Context(0)
+    try:
+        ctx.autotune(WL.scoring, j_max=8, cells_per_trial=2e7, table_path=path)
+    finally:
+        ctx.close()
+    rs = stream(6000, seed=6)
+    reqs = [rs.request(r) for r in range(rs.size.size)]
+    srv = xt.Server(0, slots=2, tuning_path=path)
+    try:
+        tickets = [srv.submit(*r, WL.scoring) for r in reqs]
+        for k, (t, req) in enumerate(zip(tickets, reqs)):
+            out, cells, _ = srv.wait(t, timeout_s=120)
+            check(out, cells, oracle_of(req, WL.scoring), f"tuned request {k}")
+    finally:
+        srv.close()
+    with pytest.raises(xt.XtError) as e:
+        xt.Server(0, slots=1, tuning_path=str(tmp_path / "missing.json"))
+    assert e.value.status == xt.XT_EINVAL

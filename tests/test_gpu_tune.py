@@ -81,7 +81,8 @@ def test_autotune_round_trip(xt, tmp_path):
     ctx = xt.Context(0)
     try:
         ctx.autotune(sc, j_max=8, cells_per_trial=3e7, table_path=path)
-        chosen = {j: ctx.bucket_schedule(sc.w, j) for j in range(5, 9)}
+        chosen = {(j, k): ctx.bucket_schedule(sc.w, j, k) for j in range(5, 9)
+                  for k in (xt.XT_BATCH_LARGE, xt.XT_BATCH_SMALL)}
         assert all(P >= 1 for P, _ in chosen.values())
         # a second band goes into the same file
         ctx.autotune(ScoringParams(w=20, zdrop=30), j_max=6, cells_per_trial=1e7, table_path=path)
@@ -91,11 +92,12 @@ def test_autotune_round_trip(xt, tmp_path):
     assert doc["format"] == "xt-tuning" and len(doc["entries"]) == 2
     e = [x for x in doc["entries"] if x["w"] == sc.w][0]
     assert [b["j"] for b in e["buckets"]] == [5, 6, 7, 8]
-    assert all(b["gcups"] > 0 for b in e["buckets"])
+    assert all(b["gcups"] > 0 and b["gcups_s"] > 0 and b["Ps"] >= 1 for b in e["buckets"])
     ctx = xt.Context(0)
     try:
         ctx.load_tuning(path)
-        assert {j: ctx.bucket_schedule(sc.w, j) for j in range(5, 9)} == chosen
+        assert {(j, k): ctx.bucket_schedule(sc.w, j, k) for j in range(5, 9)
+                for k in (xt.XT_BATCH_LARGE, xt.XT_BATCH_SMALL)} == chosen
         wl = synth.WORKLOADS["c3_mixed"]
         b = synth.generate(wl, n=4000, first=123)
         assert_same(run_gpu(ctx, b, wl.scoring), run_oracle(b, wl.scoring), "tuned")
@@ -118,5 +120,25 @@ def test_load_tuning_ignores_other_devices_and_rejects_garbage(xt, tmp_path):
             with pytest.raises(xt.XtError) as e:
                 ctx.load_tuning(p)
             assert e.value.status == xt.XT_EINVAL
+    finally:
+        ctx.close()
+
+
+def test_small_and_large_batch_classes(xt):
+    # different schedules for small and large calls; both sizes stay exact
+    wl = synth.WORKLOADS["c5_stream"]
+    small = synth.generate(wl, n=3000, first=4242)
+    large = synth.generate(wl, n=40000, first=9000)
+    ctx = xt.Context(0)
+    try:
+        for j in range(5, 12):
+            ctx.set_bucket_schedule_for(wl.scoring.w, j, xt.XT_BATCH_LARGE, 1, 8)
+            ctx.set_bucket_schedule_for(wl.scoring.w, j, xt.XT_BATCH_SMALL, 8, 8)
+        assert ctx.bucket_schedule(wl.scoring.w, 9, xt.XT_BATCH_SMALL) == (8, 8)
+        assert ctx.bucket_schedule(wl.scoring.w, 9, xt.XT_BATCH_LARGE) == (1, 8)
+        for b in (small, large):
+            assert_same(run_gpu(ctx, b, wl.scoring), run_oracle(b, wl.scoring), f"n={b.n}")
+        with pytest.raises(xt.XtError):
+            ctx.set_bucket_schedule_for(wl.scoring.w, 9, 2, 1, 8)   # no such class
     finally:
         ctx.close()
