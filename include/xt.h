@@ -109,7 +109,9 @@ xt_status xt_ctx_sync(xt_ctx* ctx, void* stream);
  * and sorts the batch into length buckets; persistent kernels then pull pairs
  * from device-side queues, each bucket with its own schedule (pairs per warp,
  * rows per lane, packed 16-bit or 32-bit arithmetic where a per-pair score
- * bound makes it exact).
+ * bound makes it exact).  The call waits on the host for the classify pass
+ * (a few hundred bytes of bucket counts come back) before it enqueues the
+ * extension kernels; those are asynchronous.
  *
  *   q_seq, t_seq       device, uint8 codes; q_bytes / t_bytes their sizes
  *   q_off, t_off       device, int64[n_pairs]
@@ -211,19 +213,22 @@ xt_status xt_ctx_set_streams(xt_ctx* ctx, int branches);
  * per pair and R rows per lane: P = 1 is the one-lane engine (one thread per
  * pair, R = 4, 8 or 16; packed 16-bit where exact), P = 2..32 the group
  * engine (P lanes of a warp per pair, R = 4 or 8, or 16 with P <= 4).
- * Schedules are kept per band w and per batch class: XT_BATCH_SMALL
- * schedules apply to calls of at most XT_SMALL_BATCH pairs (there a pair's
- * latency on its engine bounds the call), XT_BATCH_LARGE ones to larger
- * calls, and to small calls whose bucket has no small-batch schedule.  A
- * call uses the schedules set for its own scoring's w and the built-in rule
- * for buckets without one.  P = 0 removes a bucket's schedule.  XT_EINVAL if
- * (P, R) does not exist or its band ring does not fit on this device.
- * Results never depend on the schedule.  xt_ctx_set_bucket_schedule sets
- * both classes.
+ * A call classifies its pairs first and plans every non-empty bucket from
+ * the number of pairs it holds.  Schedules are kept per band w and per
+ * class of that count: XT_BATCH_SMALL schedules apply to buckets of fewer
+ * than XT_SMALL_BUCKET pairs in the call (they cannot fill the GPU, so a
+ * pair's latency on its engine decides), XT_BATCH_LARGE ones to larger
+ * buckets, and to small buckets without a small schedule.  A call uses the
+ * schedules set for its own scoring's w and the built-in rule for buckets
+ * without one (the built-in rule gives small buckets of queries over 62
+ * bases enough lanes per pair to fill the GPU).  P = 0 removes a bucket's
+ * schedule.  XT_EINVAL if (P, R) does not exist or its band ring does not
+ * fit on this device.  Results never depend on the schedule.
+ * xt_ctx_set_bucket_schedule sets both classes.
  */
 #define XT_BATCH_LARGE 0
 #define XT_BATCH_SMALL 1
-#define XT_SMALL_BATCH 32768
+#define XT_SMALL_BUCKET 8192
 xt_status xt_ctx_set_bucket_schedule(xt_ctx* ctx, int w, int j, int P, int R);
 xt_status xt_ctx_set_bucket_schedule_for(xt_ctx* ctx, int w, int j, int batch_class, int P,
                                          int R);

@@ -193,7 +193,7 @@ def xt_ctx_get_bucket_schedule(ctx: int, w: int, j: int) -> tuple[int, int, int]
     return s, P.value, R.value
 
 
-XT_BATCH_LARGE, XT_BATCH_SMALL, XT_SMALL_BATCH = 0, 1, 32768
+XT_BATCH_LARGE, XT_BATCH_SMALL, XT_SMALL_BUCKET = 0, 1, 8192
 
 
 def xt_ctx_set_bucket_schedule_for(ctx: int, w: int, j: int, batch_class: int, P: int,

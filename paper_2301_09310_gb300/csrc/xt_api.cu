@@ -132,6 +132,7 @@ xt_status get_work(xt_ctx* ctx, int32_t n, Work* w, Batch** desc) {
 struct Plan {
   Launch launch[kMaxLaunches];
   int n_launch = 0;
+  bool bad = false;   // count-aware planning met a bucket it cannot place
   JFlags jf = {};
   bool any_huge = false;
   int64_t slab = 0;
@@ -293,6 +294,137 @@ void plan_batched(xt_ctx* ctx, const Score& sc, Plan* pl, bool allow_gring = tru
   if (pl->any_huge) add_huge_launch(ctx, sc, pl);
 }
 
+// ---- count-aware planning (the batched path): classify runs first with
+// per-bucket flags that do not depend on the counts, then every non-empty
+// bucket is planned from its own pair count.
+constexpr int32_t kBucketSmall = XT_SMALL_BUCKET;  // fewer pairs: a bucket cannot fill the GPU
+constexpr int32_t kLaneSlots = 77824;    // one-lane thread slots of a full GPU (152 x 4 x 128)
+
+// Flags for classify: kJHuge where the default group ring does not fit
+// (band geometry only), kJPacked where a one-lane schedule is possible for
+// the bucket in either size class.  lane_ok[j]: that one-lane launch exists.
+void batched_flags(xt_ctx* ctx, const Score& sc, JFlags* jf, bool* lane_ok) {
+  *jf = JFlags{};
+  for (int j = 0; j < kNumJ; ++j) lane_ok[j] = false;
+  const bool saved = ctx->plan_small;
+  for (int j = kJMin; j <= kJMax; ++j) {
+    Launch L;
+    bool want = false;
+    if (ctx->forced_P) {
+      want = ctx->forced_P == 1;
+    } else {
+      for (int small = 0; small < 2; ++small) {
+        ctx->plan_small = small != 0;
+        const BucketSched* t = tuned(ctx, sc.w, j);
+        want |= t ? t->P == 1 : j <= kLaneJMax;
+      }
+      ctx->plan_small = false;
+    }
+    lane_ok[j] = want && lane_launch(ctx, sc, CLS_PACKED, j, true, &L) &&
+                 lane_launch(ctx, sc, CLS_NARROW, j, true, &L);
+    if (lane_ok[j]) jf->f[j] |= kJPacked;
+    // the default rule's answer (tuned group schedules always fit, see
+    // bucket_sched_ok, but a bucket's class must not depend on its count)
+    const int fP = ctx->forced_P;
+    int P, R, lg;
+    bool huge;
+    std::vector<TuneEntry> keep;
+    keep.swap(ctx->tuning);
+    ctx->forced_P = fP > 1 ? fP : 0;
+    bucket_schedule(ctx, j, sc.w, &P, &R, &lg, &huge, true);
+    ctx->forced_P = fP;
+    keep.swap(ctx->tuning);
+    if (huge) jf->f[j] |= kJHuge;
+  }
+  ctx->plan_small = saved;
+}
+
+Launch queue_launch(const xt_ctx* ctx, int cls, int j, int P, int R, int lg) {
+  Launch L;
+  L.cls = cls; L.j_lo = j; L.j_hi = j; L.lane = false; L.P = P; L.R = R; L.rs_log2 = lg;
+  const size_t smem = queue_smem_bytes(P, lg);
+  const int per_sm = (int)std::min<size_t>(
+      16, std::max<size_t>(1, (size_t)(220 * 1024) / std::max<size_t>(smem + 1024, 1)));
+  L.grid = ctx->num_sms * per_sm;
+  return L;
+}
+
+// Plan the DP launches from the pair count of every (class, bucket):
+// empty buckets get no launch; a bucket too small to fill the GPU takes its
+// small-batch schedule, or by default a group schedule with enough lanes per
+// pair to fill it; larger buckets take the throughput schedule.
+void plan_counts(xt_ctx* ctx, const Score& sc, const int32_t (*cnt)[kNumJ], const JFlags& jf,
+                 const bool* lane_ok, Plan* pl) {
+  pl->jf = jf;
+  const bool saved = ctx->plan_small;
+  for (int cls = CLS_PACKED; cls <= CLS_WIDE; ++cls) {
+    int prev = -1;
+    for (int j = kJMax; j >= 0; --j) {
+      const int32_t c = cnt[cls][j];
+      if (c == 0) continue;                   // empty: the launch before it may span it
+      const int jj = j < kJMin ? kJMin : j;   // classify clamps short queries into kJMin
+      ctx->plan_small = c < kBucketSmall;
+      Launch L;
+      bool lane = false;
+      if (cls != CLS_WIDE && lane_ok[jj]) {
+        lane = true;
+        if (ctx->forced_P > 1) {
+          lane = false;
+        } else if (!ctx->forced_P) {
+          const BucketSched* t = tuned(ctx, sc.w, jj);
+          if (t) lane = t->P == 1;
+          else if (ctx->plan_small && jj >= 7) lane = false;  // latency rule below
+        }
+      }
+      if (lane) {
+        lane_launch(ctx, sc, cls, jj, true, &L);
+      } else {
+        int P = 0, R = 8, lg = 0;
+        bool huge = false;
+        const BucketSched* t = ctx->forced_P ? nullptr : tuned(ctx, sc.w, jj);
+        if (!ctx->forced_P && !t && ctx->plan_small && jj >= 7 && cls != CLS_WIDE) {
+          // enough lanes per pair to fill the GPU, where the ring fits
+          int want = 4;
+          while (want < 32 && (int64_t)want * c < kLaneSlots) want *= 2;
+          for (int q = want; q >= 2 && P == 0; q /= 2) {
+            const int l = queue_ring_log2(jj, sc.w, q, 8);
+            if (l <= kQueueRsCapLog2 && queue_smem_bytes(q, l) <= (size_t)ctx->smem_optin / 2 - 1024) {
+              P = q;
+              lg = l;
+            }
+          }
+        }
+        if (P == 0) bucket_schedule(ctx, jj, sc.w, &P, &R, &lg, &huge, true);
+        if (huge) {
+          // the flags gave this bucket no HUGE class, so its pairs would be lost
+          pl->bad = true;
+          continue;
+        }
+        L = queue_launch(ctx, cls, jj, P, R, lg);
+      }
+      L.j_lo = j;
+      L.j_hi = j;
+      if (prev >= 0 && same_config(pl->launch[prev], L)) {
+        pl->launch[prev].j_lo = j;
+        continue;
+      }
+      if (pl->n_launch >= kMaxLaunches - 1) {  // 3 classes x 17 buckets + 1 stay below
+        pl->bad = true;
+        continue;
+      }
+      pl->launch[pl->n_launch] = L;
+      prev = pl->n_launch++;
+    }
+  }
+  ctx->plan_small = saved;
+  int32_t huge_pairs = 0;
+  for (int j = 0; j < kNumJ; ++j) huge_pairs += cnt[CLS_HUGE][j];
+  if (huge_pairs > 0) {
+    pl->any_huge = true;
+    add_huge_launch(ctx, sc, pl);
+  }
+}
+
 // Device bytes the global-ring launches of a plan need (they run one after
 // another on the stream and share one pool).
 size_t pool_bytes(const Plan& pl) {
@@ -357,17 +489,24 @@ xt_status check_args(xt_ctx* ctx, const void* q_seq, int64_t q_bytes, const void
   return XT_OK;
 }
 
-// Enqueue one call's work: reset counters, classify, order, extension kernels.
-cudaError_t enqueue(xt_ctx* ctx, bool plain, const Plan& pl, int plain_rs, const Score& sc,
-                    int32_t match, const Work& w, const Batch* desc, int32_t n_cap,
-                    cudaStream_t stream, int* dp_out) {
+// The front of a call: reset counters, classify, order the queue.
+cudaError_t enqueue_front(const JFlags& jf, const Score& sc, int32_t match, const Work& w,
+                          const Batch* desc, int32_t n_cap, cudaStream_t stream) {
   cudaError_t e = cudaMemsetAsync(w.counts, 0, 4 * (size_t)kNumBuckets, stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(w.heads, 0, 4 * (size_t)kMaxLaunches, stream);
-  if (e == cudaSuccess) e = launch_classify(desc, n_cap, sc, match, pl.jf, w, stream);
+  if (e == cudaSuccess) e = launch_classify(desc, n_cap, sc, match, jf, w, stream);
   if (e == cudaSuccess) e = launch_order(desc, n_cap, w, stream);
+  return e;
+}
+
+// The extension kernels of a call (and the plain kernel for the plain path).
+cudaError_t enqueue_dp(xt_ctx* ctx, bool plain, const Plan& pl, int plain_rs, const Score& sc,
+                       const Work& w, const Batch* desc, int32_t n_cap, cudaStream_t stream,
+                       int* dp_out) {
+  cudaError_t e = cudaSuccess;
   const int slot = ctx->ev_pending;
   const bool timed = ctx->timing && slot < xt_ctx::kEvRing;
-  if (e == cudaSuccess && timed) {
+  if (timed) {
     for (int k = 0; k < 2; ++k)
       if (!ctx->ev[slot][k]) cudaEventCreate(&ctx->ev[slot][k]);
     cudaEventRecord(ctx->ev[slot][0], stream);
@@ -392,6 +531,14 @@ cudaError_t enqueue(xt_ctx* ctx, bool plain, const Plan& pl, int plain_rs, const
     if (nb > 1) st = ctx->aux[L.global_ring ? 0 : (rr++ % nb)];
     e = L.lane ? launch_lane(desc, sc, w, L, i, ctx->pool, st)
                : launch_queue(desc, sc, w, L, i, ctx->pool, st);
+    if (e != cudaSuccess) {
+      char buf[192];
+      std::snprintf(buf, sizeof(buf),
+                    "launch %d of %d (%s cls %d buckets %d..%d P %d R %d ring 2^%d %s grid %d): ", i,
+                    pl.n_launch, L.lane ? "one-lane" : "group", L.cls, L.j_lo, L.j_hi, L.P, L.R,
+                    L.rs_log2, L.global_ring ? "global" : "shared", L.grid);
+      ctx->launch_error = buf;
+    }
     ++dp;
   }
   if (e == cudaSuccess && nb > 1) {
@@ -406,6 +553,25 @@ cudaError_t enqueue(xt_ctx* ctx, bool plain, const Plan& pl, int plain_rs, const
   }
   *dp_out = dp;
   return e;
+}
+
+// A signature of a plan's launches (the graph of a call depends on it).
+uint64_t plan_signature(const Plan& pl) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](int64_t v) {
+    for (int b = 0; b < 8; ++b) {
+      h ^= (uint64_t)((v >> (8 * b)) & 0xFF);
+      h *= 1099511628211ull;
+    }
+  };
+  mix(pl.n_launch);
+  for (int i = 0; i < pl.n_launch; ++i) {
+    const Launch& L = pl.launch[i];
+    mix(L.cls); mix(L.j_lo); mix(L.j_hi); mix(L.lane); mix(L.P); mix(L.R); mix(L.rs_log2);
+    mix(L.global_ring); mix(L.slab); mix(L.grid); mix(L.mparam);
+  }
+  for (int j = 0; j < kNumJ; ++j) mix(pl.jf.f[j]);
+  return h;
 }
 
 xt_status run(xt_ctx* ctx, bool plain, const uint8_t* q_seq, int64_t q_bytes, const int64_t* q_off,
@@ -426,19 +592,8 @@ xt_status run(xt_ctx* ctx, bool plain, const uint8_t* q_seq, int64_t q_bytes, co
   Batch* desc = nullptr;
   s = get_work(ctx, n_cap, &w, &desc);
   if (s != XT_OK) return s;
-  Plan pl;
-  int plain_rs = 0;
   ctx->match = scr->match;
-  ctx->plan_small = n_cap <= kSmallBatchMax;
-  if (plain) plan_plain(ctx, sc, &pl, &plain_rs);
-  else plan_batched(ctx, sc, &pl);
-  const size_t want = pool_bytes(pl);
-  if (want) {
-    void* old = ctx->pool;
-    s = dev_alloc(ctx, (void**)&ctx->pool, &ctx->pool_bytes, want);
-    if (s != XT_OK) return s;
-    if ((void*)ctx->pool != old) drop_graphs(ctx);
-  }
+  ctx->plan_small = false;
   // this call's arguments go to the device descriptor through a pinned slot
   Batch hb;
   hb.q_seq = q_seq; hb.t_seq = t_seq; hb.q_off = q_off; hb.t_off = t_off; hb.q_len = q_len;
@@ -452,6 +607,48 @@ xt_status run(xt_ctx* ctx, bool plain, const uint8_t* q_seq, int64_t q_bytes, co
   e = cudaMemcpyAsync(desc, &ctx->desc_host[slot], sizeof(Batch), cudaMemcpyHostToDevice, stream);
   if (e == cudaSuccess) e = cudaEventRecord(ctx->desc_ev[slot], stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "descriptor copy");
+
+  Plan pl;
+  int plain_rs = 0;
+  if (plain) {
+    plan_plain(ctx, sc, &pl, &plain_rs);
+  } else {
+    // phase 1: classify and order with count-independent bucket flags, then
+    // read the pair count of every (class, bucket) back to plan phase 2
+    JFlags jf;
+    bool lane_ok[kNumJ];
+    batched_flags(ctx, sc, &jf, lane_ok);
+    e = enqueue_front(jf, sc, scr->match, w, desc, n_cap, stream);
+    const size_t seg_bytes =
+        (size_t)((const char*)(w.seg_end + kNumClasses * kNumJ) - (const char*)w.seg_begin);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ctx->seg_host, w.seg_begin, seg_bytes, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->seg_ev, stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ctx->seg_ev);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "classify");
+    const int32_t* sb = ctx->seg_host;
+    const int32_t* se = ctx->seg_host + (w.seg_end - w.seg_begin);
+    int32_t cnt[kNumClasses][kNumJ];
+    for (int c = 0; c < kNumClasses; ++c)
+      for (int j = 0; j < kNumJ; ++j) cnt[c][j] = se[c * kNumJ + j] - sb[c * kNumJ + j];
+    plan_counts(ctx, sc, cnt, jf, lane_ok, &pl);
+    if (pl.bad) return fail(ctx, XT_ECUDA, "internal: inconsistent bucket plan");
+  }
+  const size_t want = pool_bytes(pl);
+  if (want) {
+    void* old = ctx->pool;
+    s = dev_alloc(ctx, (void**)&ctx->pool, &ctx->pool_bytes, want);
+    if (s != XT_OK) return s;
+    if ((void*)ctx->pool != old) drop_graphs(ctx);
+  }
+  // the plain path's whole call, or the batched path's extension kernels,
+  // replay as one graph once a call with the same key has been seen
+  auto body = [&](cudaStream_t st, int* dp) -> cudaError_t {
+    cudaError_t r = cudaSuccess;
+    if (plain) r = enqueue_front(pl.jf, sc, scr->match, w, desc, n_cap, st);
+    if (r == cudaSuccess) r = enqueue_dp(ctx, plain, pl, plain_rs, sc, w, desc, n_cap, st, dp);
+    return r;
+  };
   int dp = 0;
   GraphEntry* ge = nullptr;
   if (ctx->graphs && !ctx->timing) {
@@ -460,23 +657,24 @@ xt_status run(xt_ctx* ctx, bool plain, const uint8_t* q_seq, int64_t q_bytes, co
     key.plain = plain; key.sc = *scr; key.forced_P = ctx->forced_P; key.forced_R = ctx->forced_R;
     key.n_cap_log2 = n_cap_log2; key.work = ctx->work; key.pool = ctx->pool;
     key.has_cells = cells != nullptr;
+    key.plan_sig = plan_signature(pl);
+    key.branches = ctx->branches;
     for (auto& g : ctx->graph_cache)
       if (g.key == key) ge = &g;
     if (!ge) {
-      if (ctx->graph_cache.size() >= 32) drop_graphs(ctx);
+      if (ctx->graph_cache.size() >= 64) drop_graphs(ctx);
       ctx->graph_cache.push_back(GraphEntry());
       ge = &ctx->graph_cache.back();
       ge->key = key;
     }
     ge->seen += 1;
     if (!ge->exec && ge->seen >= 2) {
-      // capture this call's launches once on a private stream; the graph reads
-      // every per-call argument from the device descriptor
+      // capture once on a private stream; the graph reads every per-call
+      // argument from the device descriptor
       cudaGraph_t g = nullptr;
       e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        cudaError_t e2 = enqueue(ctx, plain, pl, plain_rs, sc, scr->match, w, desc, n_cap,
-                                 ctx->cap_stream, &dp);
+        cudaError_t e2 = body(ctx->cap_stream, &dp);
         e = cudaStreamEndCapture(ctx->cap_stream, &g);
         if (e == cudaSuccess) e = e2;
       }
@@ -497,8 +695,9 @@ xt_status run(xt_ctx* ctx, bool plain, const uint8_t* q_seq, int64_t q_bytes, co
     if (e != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
     dp = plain ? 1 + pl.n_launch : pl.n_launch;
   } else {
-    e = enqueue(ctx, plain, pl, plain_rs, sc, scr->match, w, desc, n_cap, stream, &dp);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "launch");
+    ctx->launch_error.clear();
+    e = body(stream, &dp);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, ("launch " + ctx->launch_error).c_str());
   }
   ctx->calls += 1;
   ctx->launches += 3 + dp;  // classify, scan, scatter + DP kernels
@@ -529,6 +728,8 @@ xt_status xt_ctx_create(xt_ctx** out, int device, size_t mem_budget_bytes) {
   for (int k = 0; ok && k < kDescSlots; ++k)
     ok = cudaEventCreateWithFlags(&c->desc_ev[k], cudaEventDisableTiming) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+  ok = ok && cudaHostAlloc((void**)&c->seg_host, 4096, cudaHostAllocDefault) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&c->seg_ev, cudaEventDisableTiming) == cudaSuccess;
   ok = ok && cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) == cudaSuccess;
   for (int b = 0; ok && b < kMaxBranches; ++b) {
     ok = cudaStreamCreateWithFlags(&c->aux[b], cudaStreamNonBlocking) == cudaSuccess &&
@@ -558,6 +759,8 @@ xt_status xt_ctx_destroy(xt_ctx* ctx) {
     if (e) cudaEventDestroy(e);
   if (ctx->desc_host) cudaFreeHost(ctx->desc_host);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->seg_host) cudaFreeHost(ctx->seg_host);
+  if (ctx->seg_ev) cudaEventDestroy(ctx->seg_ev);
   if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
   for (int b = 0; b < kMaxBranches; ++b) {
     if (ctx->aux[b]) cudaStreamDestroy(ctx->aux[b]);

@@ -20,6 +20,8 @@ struct GraphKey {
   void* work;
   void* pool;
   bool has_cells;
+  uint64_t plan_sig;   // the plan of the extension kernels (count-aware)
+  int branches;
   bool operator==(const GraphKey& o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
 };
 struct GraphEntry {
@@ -35,11 +37,10 @@ constexpr int kMaxBranches = 8;  // streams the DP launches of one call fork ont
 struct BucketSched {
   int P = 0, R = 0;
 };
-// The schedules of every bucket for calls whose band is w: one set for large
-// calls (tuned at saturation) and one for calls of at most kSmallBatchMax
-// pairs (tuned on small trials: there a pair's latency on its engine, not
-// the engine's throughput, decides the call's time).
-constexpr int32_t kSmallBatchMax = XT_SMALL_BATCH;
+// The schedules of every bucket for calls whose band is w: one set for
+// buckets that fill the GPU (tuned at saturation) and one for buckets of
+// fewer than XT_SMALL_BUCKET pairs in a call (tuned on small trials: there a
+// pair's latency on its engine, not the engine's throughput, decides).
 struct TuneEntry {
   int w = 0;
   BucketSched b[kNumJ];
@@ -92,8 +93,12 @@ struct xt_ctx {
   int forced_P = 0;              // schedule override (0: per-bucket table)
   int forced_R = 0;
   std::vector<xt::TuneEntry> tuning;  // per-band bucket schedules (xt_autotune)
-  bool plan_small = false;       // the call being planned has at most kSmallBatchMax pairs
+  bool plan_small = false;       // the bucket being planned is small (its small-batch schedule)
+  // pair counts per (class, bucket) read back between classify and the plan
+  int32_t* seg_host = nullptr;
+  cudaEvent_t seg_ev = nullptr;
   std::mutex mu;
   std::string last_error;
+  std::string launch_error;      // which launch of the call failed
 };
 

@@ -307,6 +307,11 @@ __global__ void __launch_bounds__(32) k_plain(const Batch* __restrict__ bd, Scor
 }
 
 // ---------------------------------------------------------------- launchers
+// Static shared memory of the kernels (descriptor copy, profiles) stays below
+// this; a launch asks for the larger dynamic limit whenever both together
+// could pass the 48 KB a kernel gets without opting in.
+constexpr size_t kStaticSmemMax = 1024;
+
 cudaError_t launch_classify(const Batch* bd, int32_t n_cap, const Score& sc, int32_t match,
                             const JFlags& jf, const Work& w, cudaStream_t stream) {
   if (n_cap == 0) return cudaSuccess;
@@ -335,7 +340,7 @@ static cudaError_t launch_queue_t(const Batch* b, const Score& sc, const Work& w
                                   int head_id, int2* gring, cudaStream_t stream) {
   const size_t smem = L.global_ring ? 0 : queue_smem_bytes(P, L.rs_log2);
   auto kern = k_queue<P, R, WIDE>;
-  if (smem > 48 * 1024) {
+  if (smem + kStaticSmemMax > 48 * 1024) {  // the default limit covers static + dynamic
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -378,7 +383,7 @@ static cudaError_t launch_lane_t(const Batch* b, const Score& sc, const Work& w,
   const size_t smem = (GRING ? 0 : kLaneThreads * lane_ring_bytes(L.cls, L.rs_log2)) +
                       (QSTAGE ? lane_stage_bytes(L.j_hi) : 0);
   auto kern = k_lane<R, PACKED, GRING, QSTAGE>;
-  if (smem > 48 * 1024) {
+  if (smem + kStaticSmemMax > 48 * 1024) {  // the default limit covers static + dynamic
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -420,7 +425,7 @@ cudaError_t launch_plain(const Batch* b, int32_t n_cap, const Score& sc, const W
                          int rs_log2, cudaStream_t stream) {
   if (n_cap == 0) return cudaSuccess;
   const size_t smem = ((size_t)1 << rs_log2) * sizeof(int2);
-  if (smem > 48 * 1024) {
+  if (smem + kStaticSmemMax > 48 * 1024) {  // the default limit covers static + dynamic
     cudaError_t e = cudaFuncSetAttribute(k_plain, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
