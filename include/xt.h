@@ -133,6 +133,24 @@ xt_status xt_extend_batch(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_bytes,
                           xt_result* out, int64_t* cells_out, void* stream);
 
 /*
+ * xt_extend_batch in two steps, for callers that must not block (one
+ * thread driving several contexts and streams).  _begin checks the
+ * arguments (errors as xt_extend_batch) and enqueues the classify pass and
+ * the copy of its bucket counts on `stream`; _ready sets *ready = 1 once
+ * those counts are on the host; _finish plans and enqueues the extension
+ * kernels (waiting for the counts if they are not there yet).  Between
+ * _begin and _finish the context holds the call: other calls on it return
+ * XT_EBUSY.  xt_extend_batch is _begin followed by _finish.
+ */
+xt_status xt_extend_batch_begin(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_bytes,
+                                const int64_t* q_off, const int32_t* q_len, const uint8_t* t_seq,
+                                int64_t t_bytes, const int64_t* t_off, const int32_t* t_len,
+                                const int32_t* h0, int32_t n_pairs, const xt_scoring* sc,
+                                xt_result* out, int64_t* cells_out, void* stream);
+xt_status xt_extend_batch_ready(xt_ctx* ctx, int* ready);
+xt_status xt_extend_batch_finish(xt_ctx* ctx);
+
+/*
  * Plain extension: one pair per thread block (one warp), 32-bit arithmetic,
  * no bucketing and no persistent queue -- the comparison kernel.  Same
  * arguments, conventions and results as xt_extend_batch.

@@ -28,7 +28,8 @@ EXPORTED = ("xt_ctx_create", "xt_ctx_destroy", "xt_ctx_sync", "xt_extend_batch",
             "xt_serve_pause", "xt_serve_get_stats", "xt_serve_destroy", "xt_ctx_set_streams",
             "xt_ctx_set_bucket_schedule", "xt_ctx_get_bucket_schedule", "xt_autotune",
             "xt_ctx_load_tuning", "xt_ctx_set_bucket_schedule_for",
-            "xt_ctx_get_bucket_schedule_for")
+            "xt_ctx_get_bucket_schedule_for", "xt_extend_batch_begin", "xt_extend_batch_ready",
+            "xt_extend_batch_finish")
 XT_STATIC_MAX_PAIRS = 1 << 20
 
 
@@ -95,8 +96,14 @@ def load_library(path: str | None = None):
     lib.xt_ctx_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.c_size_t]
     lib.xt_ctx_destroy.argtypes = [P]
     lib.xt_ctx_sync.argtypes = [P, P]
-    for fn in ("xt_extend_batch", "xt_extend_batch_plain", "xt_extend_batch_host"):
+    for fn in ("xt_extend_batch", "xt_extend_batch_plain", "xt_extend_batch_host",
+               "xt_extend_batch_begin"):
         getattr(lib, fn).argtypes = batch_args
+    lib.xt_extend_batch_begin.restype = ctypes.c_int
+    lib.xt_extend_batch_ready.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
+    lib.xt_extend_batch_ready.restype = ctypes.c_int
+    lib.xt_extend_batch_finish.argtypes = [P]
+    lib.xt_extend_batch_finish.restype = ctypes.c_int
     for fn in ("xt_ctx_create", "xt_ctx_destroy", "xt_ctx_sync", "xt_extend_batch",
                "xt_extend_batch_plain", "xt_extend_batch_host"):
         getattr(lib, fn).restype = ctypes.c_int
@@ -150,7 +157,8 @@ def load_library(path: str | None = None):
                "xt_serve_pause", "xt_serve_get_stats", "xt_serve_destroy", "xt_ctx_set_streams",
             "xt_ctx_set_bucket_schedule", "xt_ctx_get_bucket_schedule", "xt_autotune",
             "xt_ctx_load_tuning", "xt_ctx_set_bucket_schedule_for",
-            "xt_ctx_get_bucket_schedule_for"):
+            "xt_ctx_get_bucket_schedule_for", "xt_extend_batch_begin", "xt_extend_batch_ready",
+            "xt_extend_batch_finish"):
         getattr(lib, fn).restype = ctypes.c_int
     _LIB = lib
     return lib
@@ -331,6 +339,22 @@ def xt_extend_batch_host(ctx, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_of
                          sc, out, cells, stream) -> int:
     return _call("xt_extend_batch_host", ctx, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off,
                  t_len, h0, n, sc, out, cells, stream)
+
+
+def xt_extend_batch_begin(ctx, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off, t_len, h0, n,
+                          sc, out, cells, stream) -> int:
+    return _call("xt_extend_batch_begin", ctx, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes,
+                 t_off, t_len, h0, n, sc, out, cells, stream)
+
+
+def xt_extend_batch_ready(ctx) -> tuple[int, bool]:
+    r = ctypes.c_int(0)
+    s = load_library().xt_extend_batch_ready(ctypes.c_void_p(ctx), ctypes.byref(r))
+    return s, bool(r.value)
+
+
+def xt_extend_batch_finish(ctx) -> int:
+    return load_library().xt_extend_batch_finish(ctypes.c_void_p(ctx))
 
 
 def xt_extend_batch_static(q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off, t_len, h0, n, sc,

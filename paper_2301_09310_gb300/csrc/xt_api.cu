@@ -574,23 +574,36 @@ uint64_t plan_signature(const Plan& pl) {
   return h;
 }
 
-xt_status run(xt_ctx* ctx, bool plain, const uint8_t* q_seq, int64_t q_bytes, const int64_t* q_off,
-              const int32_t* q_len, const uint8_t* t_seq, int64_t t_bytes, const int64_t* t_off,
-              const int32_t* t_len, const int32_t* h0, int32_t n, const xt_scoring* scr,
-              xt_result* out, int64_t* cells, cudaStream_t stream) {
+// The first half of a call: checks, workspace, descriptor, and for the
+// batched path the classify pass and the copy of its bucket counts.  The
+// call's state waits in ctx->pending for run_finish.
+xt_status run_begin(xt_ctx* ctx, bool plain, const uint8_t* q_seq, int64_t q_bytes,
+                    const int64_t* q_off, const int32_t* q_len, const uint8_t* t_seq,
+                    int64_t t_bytes, const int64_t* t_off, const int32_t* t_len,
+                    const int32_t* h0, int32_t n, const xt_scoring* scr, xt_result* out,
+                    int64_t* cells, cudaStream_t stream) {
   xt_status s = check_args(ctx, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off, t_len, h0, n,
                            scr, out);
   if (s != XT_OK) return s;
-  if (n == 0) return XT_OK;
+  if (ctx->pending.active) return fail(ctx, XT_EBUSY, "a begun call has not been finished");
+  PendingCall& pc = ctx->pending;
+  pc = PendingCall();
+  pc.n = n;
+  if (n == 0) {
+    pc.active = true;  // finish has nothing to do
+    return XT_OK;
+  }
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
-  const Score sc = make_score(scr);
-  int n_cap_log2 = 10;
-  while ((1 << n_cap_log2) < n) ++n_cap_log2;
-  const int32_t n_cap = n_cap_log2 >= 31 ? INT32_MAX : (1 << n_cap_log2);
-  Work w;
-  Batch* desc = nullptr;
-  s = get_work(ctx, n_cap, &w, &desc);
+  pc.plain = plain;
+  pc.scr = *scr;
+  pc.sc = make_score(scr);
+  pc.n_cap_log2 = 10;
+  while ((1 << pc.n_cap_log2) < n) ++pc.n_cap_log2;
+  pc.n_cap = pc.n_cap_log2 >= 31 ? INT32_MAX : (1 << pc.n_cap_log2);
+  pc.has_cells = cells != nullptr;
+  pc.stream = stream;
+  s = get_work(ctx, pc.n_cap, &pc.w, &pc.desc);
   if (s != XT_OK) return s;
   ctx->match = scr->match;
   ctx->plan_small = false;
@@ -604,40 +617,59 @@ xt_status run(xt_ctx* ctx, bool plain, const uint8_t* q_seq, int64_t q_bytes, co
   e = cudaEventSynchronize(ctx->desc_ev[slot]);  // that slot's previous copy has run
   if (e != cudaSuccess) return cuda_fail(ctx, e, "descriptor slot");
   ctx->desc_host[slot] = hb;
-  e = cudaMemcpyAsync(desc, &ctx->desc_host[slot], sizeof(Batch), cudaMemcpyHostToDevice, stream);
+  e = cudaMemcpyAsync(pc.desc, &ctx->desc_host[slot], sizeof(Batch), cudaMemcpyHostToDevice,
+                      stream);
   if (e == cudaSuccess) e = cudaEventRecord(ctx->desc_ev[slot], stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "descriptor copy");
+  if (!plain) {
+    // classify and order with count-independent bucket flags, then bring the
+    // pair count of every (class, bucket) back for the plan
+    batched_flags(ctx, pc.sc, &pc.jf, pc.lane_ok);
+    e = enqueue_front(pc.jf, pc.sc, scr->match, pc.w, pc.desc, pc.n_cap, stream);
+    const size_t seg_bytes =
+        (size_t)((const char*)(pc.w.seg_end + kNumClasses * kNumJ) - (const char*)pc.w.seg_begin);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ctx->seg_host, pc.w.seg_begin, seg_bytes, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->seg_ev, stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "classify");
+  }
+  pc.active = true;
+  return XT_OK;
+}
 
+// The second half: plan from the counts (waiting for them if needed) and
+// enqueue the extension kernels, through a captured graph when one exists.
+xt_status run_finish(xt_ctx* ctx) {
+  PendingCall& pc = ctx->pending;
+  if (!pc.active) return fail(ctx, XT_EINVAL, "no begun call to finish");
+  pc.active = false;
+  if (pc.n == 0) return XT_OK;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+  const bool plain = pc.plain;
+  const Score& sc = pc.sc;
+  const Work& w = pc.w;
+  ctx->match = pc.scr.match;
   Plan pl;
   int plain_rs = 0;
   if (plain) {
+    ctx->plan_small = false;
     plan_plain(ctx, sc, &pl, &plain_rs);
   } else {
-    // phase 1: classify and order with count-independent bucket flags, then
-    // read the pair count of every (class, bucket) back to plan phase 2
-    JFlags jf;
-    bool lane_ok[kNumJ];
-    batched_flags(ctx, sc, &jf, lane_ok);
-    e = enqueue_front(jf, sc, scr->match, w, desc, n_cap, stream);
-    const size_t seg_bytes =
-        (size_t)((const char*)(w.seg_end + kNumClasses * kNumJ) - (const char*)w.seg_begin);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(ctx->seg_host, w.seg_begin, seg_bytes, cudaMemcpyDeviceToHost, stream);
-    if (e == cudaSuccess) e = cudaEventRecord(ctx->seg_ev, stream);
-    if (e == cudaSuccess) e = cudaEventSynchronize(ctx->seg_ev);
+    e = cudaEventSynchronize(ctx->seg_ev);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "classify");
     const int32_t* sb = ctx->seg_host;
     const int32_t* se = ctx->seg_host + (w.seg_end - w.seg_begin);
     int32_t cnt[kNumClasses][kNumJ];
     for (int c = 0; c < kNumClasses; ++c)
       for (int j = 0; j < kNumJ; ++j) cnt[c][j] = se[c * kNumJ + j] - sb[c * kNumJ + j];
-    plan_counts(ctx, sc, cnt, jf, lane_ok, &pl);
+    plan_counts(ctx, sc, cnt, pc.jf, pc.lane_ok, &pl);
     if (pl.bad) return fail(ctx, XT_ECUDA, "internal: inconsistent bucket plan");
   }
   const size_t want = pool_bytes(pl);
   if (want) {
     void* old = ctx->pool;
-    s = dev_alloc(ctx, (void**)&ctx->pool, &ctx->pool_bytes, want);
+    xt_status s = dev_alloc(ctx, (void**)&ctx->pool, &ctx->pool_bytes, want);
     if (s != XT_OK) return s;
     if ((void*)ctx->pool != old) drop_graphs(ctx);
   }
@@ -645,8 +677,8 @@ xt_status run(xt_ctx* ctx, bool plain, const uint8_t* q_seq, int64_t q_bytes, co
   // replay as one graph once a call with the same key has been seen
   auto body = [&](cudaStream_t st, int* dp) -> cudaError_t {
     cudaError_t r = cudaSuccess;
-    if (plain) r = enqueue_front(pl.jf, sc, scr->match, w, desc, n_cap, st);
-    if (r == cudaSuccess) r = enqueue_dp(ctx, plain, pl, plain_rs, sc, w, desc, n_cap, st, dp);
+    if (plain) r = enqueue_front(pl.jf, sc, pc.scr.match, w, pc.desc, pc.n_cap, st);
+    if (r == cudaSuccess) r = enqueue_dp(ctx, plain, pl, plain_rs, sc, w, pc.desc, pc.n_cap, st, dp);
     return r;
   };
   int dp = 0;
@@ -654,9 +686,9 @@ xt_status run(xt_ctx* ctx, bool plain, const uint8_t* q_seq, int64_t q_bytes, co
   if (ctx->graphs && !ctx->timing) {
     GraphKey key;
     std::memset(&key, 0, sizeof(key));
-    key.plain = plain; key.sc = *scr; key.forced_P = ctx->forced_P; key.forced_R = ctx->forced_R;
-    key.n_cap_log2 = n_cap_log2; key.work = ctx->work; key.pool = ctx->pool;
-    key.has_cells = cells != nullptr;
+    key.plain = plain; key.sc = pc.scr; key.forced_P = ctx->forced_P; key.forced_R = ctx->forced_R;
+    key.n_cap_log2 = pc.n_cap_log2; key.work = ctx->work; key.pool = ctx->pool;
+    key.has_cells = pc.has_cells;
     key.plan_sig = plan_signature(pl);
     key.branches = ctx->branches;
     for (auto& g : ctx->graph_cache)
@@ -691,18 +723,31 @@ xt_status run(xt_ctx* ctx, bool plain, const uint8_t* q_seq, int64_t q_bytes, co
     }
   }
   if (ge && ge->exec) {
-    e = cudaGraphLaunch(ge->exec, stream);
+    e = cudaGraphLaunch(ge->exec, pc.stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
     dp = plain ? 1 + pl.n_launch : pl.n_launch;
   } else {
     ctx->launch_error.clear();
-    e = body(stream, &dp);
+    e = body(pc.stream, &dp);
     if (e != cudaSuccess) return cuda_fail(ctx, e, ("launch " + ctx->launch_error).c_str());
   }
   ctx->calls += 1;
   ctx->launches += 3 + dp;  // classify, scan, scatter + DP kernels
   ctx->dp_launches += dp;
   return XT_OK;
+}
+
+xt_status run(xt_ctx* ctx, bool plain, const uint8_t* q_seq, int64_t q_bytes, const int64_t* q_off,
+              const int32_t* q_len, const uint8_t* t_seq, int64_t t_bytes, const int64_t* t_off,
+              const int32_t* t_len, const int32_t* h0, int32_t n, const xt_scoring* scr,
+              xt_result* out, int64_t* cells, cudaStream_t stream) {
+  xt_status s = run_begin(ctx, plain, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off, t_len,
+                          h0, n, scr, out, cells, stream);
+  if (s != XT_OK) {
+    if (s != XT_EBUSY) ctx->pending.active = false;
+    return s;
+  }
+  return run_finish(ctx);
 }
 
 }  // namespace
@@ -786,6 +831,43 @@ xt_status xt_extend_batch(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_bytes,
   std::lock_guard<std::mutex> lk(ctx->mu);
   return run(ctx, false, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off, t_len, h0, n_pairs,
              sc, out, cells_out, (cudaStream_t)stream);
+}
+
+xt_status xt_extend_batch_begin(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_bytes,
+                                const int64_t* q_off, const int32_t* q_len, const uint8_t* t_seq,
+                                int64_t t_bytes, const int64_t* t_off, const int32_t* t_len,
+                                const int32_t* h0, int32_t n_pairs, const xt_scoring* sc,
+                                xt_result* out, int64_t* cells_out, void* stream) {
+  if (!ctx) return XT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  const xt_status s = run_begin(ctx, false, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off,
+                                t_len, h0, n_pairs, sc, out, cells_out, (cudaStream_t)stream);
+  if (s != XT_OK && s != XT_EBUSY) ctx->pending.active = false;
+  return s;
+}
+
+xt_status xt_extend_batch_ready(xt_ctx* ctx, int* ready) {
+  if (!ctx || !ready) return XT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (!ctx->pending.active) return fail(ctx, XT_EINVAL, "no begun call");
+  if (ctx->pending.n == 0 || ctx->pending.plain) {
+    *ready = 1;
+    return XT_OK;
+  }
+  const cudaError_t e = cudaEventQuery(ctx->seg_ev);
+  if (e == cudaErrorNotReady) {
+    *ready = 0;
+    return XT_OK;
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "classify");
+  *ready = 1;
+  return XT_OK;
+}
+
+xt_status xt_extend_batch_finish(xt_ctx* ctx) {
+  if (!ctx) return XT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  return run_finish(ctx);
 }
 
 xt_status xt_extend_batch_plain(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_bytes,

@@ -53,6 +53,23 @@ bool bucket_sched_ok(const struct ::xt_ctx* ctx, int w, int j, int P, int R);
 // Drop every captured graph of the context.
 void drop_graphs(struct ::xt_ctx* ctx);
 
+// A call between its classify pass and its extension kernels.
+struct PendingCall {
+  bool active = false;
+  bool plain = false;
+  int32_t n = 0;
+  xt_scoring scr{};
+  Score sc{};
+  Work w{};
+  Batch* desc = nullptr;
+  int32_t n_cap = 0;
+  int n_cap_log2 = 0;
+  bool has_cells = false;
+  cudaStream_t stream = nullptr;
+  JFlags jf{};
+  bool lane_ok[kNumJ] = {};
+};
+
 }  // namespace xt
 
 struct xt_ctx {
@@ -100,5 +117,6 @@ struct xt_ctx {
   std::mutex mu;
   std::string last_error;
   std::string launch_error;      // which launch of the call failed
+  xt::PendingCall pending;       // xt_extend_batch_begin .. _finish
 };
 

@@ -220,3 +220,34 @@ def test_equal_length_unbanded(ctx, L):
             assert_same(run_gpu(other, b, wl.scoring), want, f"x2 {L} P{P}R{R}")
     finally:
         other.close()
+
+
+def test_two_step_call(ctx):
+    # xt_extend_batch_begin / _ready / _finish give the one-call results; the
+    # context refuses a second call while one is pending
+    import time
+    import torch
+    import paper_2301_09310_gb300 as xt
+    from tests.gpu_util import to_dev
+    wl = synth.WORKLOADS["c5_stream"]
+    b = synth.generate(wl, n=5000, first=31337)
+    d = to_dev(b, torch.device("cuda", ctx.device))
+    out = torch.empty((b.n, 7), dtype=torch.int32, device="cuda")
+    cells = torch.empty(b.n, dtype=torch.int64, device="cuda")
+    st = torch.cuda.current_stream()
+    args = (d[0].data_ptr(), d[0].numel(), d[1].data_ptr(), d[2].data_ptr(), d[3].data_ptr(),
+            d[3].numel(), d[4].data_ptr(), d[5].data_ptr(), d[6].data_ptr(), b.n,
+            xt._scoring(wl.scoring), out.data_ptr(), cells.data_ptr(), st.cuda_stream)
+    assert xt.xt_extend_batch_begin(ctx.handle, *args) == xt.XT_OK
+    assert xt.xt_extend_batch(ctx.handle, *args) == xt.XT_EBUSY
+    for _ in range(20000):
+        s, ready = xt.xt_extend_batch_ready(ctx.handle)
+        assert s == xt.XT_OK
+        if ready:
+            break
+        time.sleep(0.0005)
+    assert ready
+    assert xt.xt_extend_batch_finish(ctx.handle) == xt.XT_OK
+    assert xt.xt_extend_batch_finish(ctx.handle) == xt.XT_EINVAL
+    torch.cuda.synchronize()
+    assert_same((out.cpu().numpy(), cells.cpu().numpy()), run_oracle(b, wl.scoring), "two-step")
