@@ -78,6 +78,10 @@ def parse_args():
     ap.add_argument("--streams", type=int, default=0,
                     help="streams the extension kernels of a call fork onto (0: library default)")
     ap.add_argument("--serve-slots", type=int, default=3)
+    ap.add_argument("--serve-batch-mib", type=int, default=128,
+                    help="staged bytes per batch (the slot capacity), MiB")
+    ap.add_argument("--serve-budget-gb", type=float, default=40.0,
+                    help="device memory budget of the whole server, GB")
     ap.add_argument("--serve-gather-threads", type=int, default=0, help="0: library default")
     return ap.parse_args()
 
@@ -567,7 +571,8 @@ def serve_leg(args, local, stream):
     return {"workload": f"c5_stream: {args.serve_pairs:,} pairs, qlen lognormal median 120 "
                         "sigma 1 clipped [1,2000], tlen = qlen + 200; requests U[1,4096] "
                         "pairs, Poisson arrivals",
-            "api": f"xt_serve_submit/xt_serve_wait (host buffers; {args.serve_slots} slots, "
+            "api": f"xt_serve_submit/xt_serve_wait (host buffers; {args.serve_slots} slots of "
+                   f"{args.serve_batch_mib} MiB, device budget {args.serve_budget_gb:g} GB, "
                    f"gather threads {args.serve_gather_threads or 'default'})",
             "latency": "scheduled arrival -> results in host memory",
             "schedules": "levels: built-in count-aware schedules (the server's default); "
@@ -607,8 +612,8 @@ def serve_levels(args, local, b, wl, peak_pairs, ref_out, ref_cells, total_cells
                           ctypes.c_void_p(out.ctypes.data + 28 * a),
                           ctypes.c_void_p(cells.ctypes.data + 8 * a)))
         srv = xt.xt_serve_create(local, xt.xt_serve_config(
-            args.serve_slots, 0, 0, 0, 0, args.serve_gather_threads,
-            table.encode() if table else None))
+            args.serve_slots, 0, args.serve_batch_mib << 20, 0, int(args.serve_budget_gb * 1e9),
+            args.serve_gather_threads, table.encode() if table else None))
         tickets = queue.Queue()
         stamps = np.zeros((nreq, 4), np.int64)   # arrival, submit, launch, done
         bpairs = np.zeros(nreq, np.int64)
