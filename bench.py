@@ -316,11 +316,38 @@ def run_xt(args):
     tuning = None
     j_max = max(5, int(np.ceil(np.log2(int(b.q_len.max()) + 2))))
     if args.tune == "auto":
+        # tune the workload's buckets, then keep the tuned table only if it
+        # beats the built-in rule on the workload itself (the tuner's trials
+        # are synthetic and one bucket at a time)
         t0 = time.perf_counter()
         ctx.autotune(wl.scoring, j_max=j_max)
-        tuning = {"seconds": round(time.perf_counter() - t0, 2),
-                  "schedule": {f"j{j}": "P{}R{}".format(*ctx.bucket_schedule(wl.scoring.w, j))
-                               for j in range(5, j_max + 1)}}
+        tune_s = time.perf_counter() - t0
+        sched = {f"j{j}": "P{}R{}".format(*ctx.bucket_schedule(wl.scoring.w, j))
+                 for j in range(5, j_max + 1)}
+        builtin = xt.Context(local)
+        if args.streams:
+            builtin.set_streams(args.streams)
+
+        def step_ms(c, reps=3):
+            for _ in range(2):
+                c.extend(*d, wl.scoring, out=out, cells=cells, stream=stream)
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                c.extend(*d, wl.scoring, out=out, cells=cells, stream=stream)
+            z.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(z) / reps
+
+        tuned_ms, builtin_ms = step_ms(ctx), step_ms(builtin)
+        kept = "tuned table"
+        if builtin_ms < tuned_ms:
+            ctx.close()
+            ctx, kept = builtin, "built-in rule"
+        else:
+            builtin.close()
+        tuning = {"seconds": round(tune_s, 2), "schedule": sched, "kept": kept,
+                  "step_ms_tuned": round(tuned_ms, 3), "step_ms_builtin": round(builtin_ms, 3)}
 
     def step(plain=False):
         ctx.extend(*d, wl.scoring, plain=plain, out=out, cells=cells, stream=stream)

@@ -238,8 +238,9 @@ xt_status xt_ctx_set_streams(xt_ctx* ctx, int branches);
  * pair's latency on its engine decides), XT_BATCH_LARGE ones to larger
  * buckets, and to small buckets without a small schedule.  A call uses the
  * schedules set for its own scoring's w and the built-in rule for buckets
- * without one (the built-in rule gives small buckets of queries over 62
- * bases enough lanes per pair to fill the GPU).  P = 0 removes a bucket's
+ * without one (one lane per pair where the bucket is large enough: 8192
+ * pairs for queries of 63..510 bases, 32768 above; otherwise enough lanes
+ * per pair to fill the GPU).  P = 0 removes a bucket's
  * schedule.  XT_EINVAL if (P, R) does not exist or its band ring does not
  * fit on this device.  Results never depend on the schedule.
  * xt_ctx_set_bucket_schedule sets both classes.
@@ -263,7 +264,9 @@ xt_status xt_ctx_get_bucket_schedule_for(xt_ctx* ctx, int w, int j, int batch_cl
  * keeps the fastest as the bucket's schedule for sc->w on this context.  A
  * trial batch holds enough pairs to fill the GPU four times over with the
  * one-lane engine (throughput at saturation), but at most about
- * cells_per_trial useful cells (0 = 3e10).  When
+ * cells_per_trial useful cells (0 = 3e10); for long queries, where that
+ * budget would leave the one-lane engine half idle, one full wave of pairs
+ * is timed instead, over the one-lane and 16/32-lane schedules only.  When
  * table_path is not NULL the schedules are also written to that JSON file
  * (entries of other devices or bands in it are kept), for
  * xt_ctx_load_tuning.  Every schedule tried must give bit-identical results

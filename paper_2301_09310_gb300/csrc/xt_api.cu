@@ -215,14 +215,18 @@ void add_huge_launch(xt_ctx* ctx, const Score& sc, Plan* pl) {
   L.rs_log2 = 0; L.global_ring = true; L.slab = pl->slab; L.grid = (int)grid; L.mparam = 0;
 }
 
-constexpr int kLaneJMax = 9;           // one-lane engine for queries up to 2^9 - 2 bases
+constexpr int kLaneJMax = 9;           // single-phase plan: one-lane engine up to 2^9 - 2 bases
+// one-lane rows per strip without a tuned schedule: 16 above 510 bases (the
+// long buckets' strips amortise their start over more rows)
+inline int lane_default_R(int j) { return j >= 10 ? 16 : 8; }
 constexpr size_t kLaneSmemCap = 48 * 1024;
 
 // One-lane launch of bucket j for class cls (PACKED or NARROW); false if it
 // needs a global ring and those are not allowed.
 bool lane_launch(xt_ctx* ctx, const Score& sc, int cls, int j, bool allow_gring, Launch* L) {
   const BucketSched* t = tuned(ctx, sc.w, j);
-  const int R = ctx->forced_P == 1 ? ctx->forced_R : (t && t->P == 1 ? t->R : 8);
+  const int R = ctx->forced_P == 1 ? ctx->forced_R
+                                    : (t && t->P == 1 ? t->R : lane_default_R(j));
   const int rows = cls == CLS_PACKED ? 2 * R : R;
   const int64_t need = std::min<int64_t>((int64_t)1 << j, next_pow2(rows + 2 * (int64_t)sc.w + 2));
   const int lg = log2_ceil(need);
@@ -299,6 +303,11 @@ void plan_batched(xt_ctx* ctx, const Score& sc, Plan* pl, bool allow_gring = tru
 // bucket is planned from its own pair count.
 constexpr int32_t kBucketSmall = XT_SMALL_BUCKET;  // fewer pairs: a bucket cannot fill the GPU
 constexpr int32_t kLaneSlots = 77824;    // one-lane thread slots of a full GPU (152 x 4 x 128)
+// Built-in rule: the fewest pairs of a bucket for one lane per pair.  A pair's
+// time on one lane grows with its length, so a bucket of long queries needs
+// close to a full wave of pairs before the one-lane engine pays; short ones
+// finish fast even when a bucket leaves most lanes idle.
+inline int32_t lane_min_pairs(int j) { return j >= 10 ? 32768 : (j >= 7 ? kBucketSmall : 0); }
 
 // Flags for classify: kJHuge where the default group ring does not fit
 // (band geometry only), kJPacked where a one-lane schedule is possible for
@@ -316,7 +325,9 @@ void batched_flags(xt_ctx* ctx, const Score& sc, JFlags* jf, bool* lane_ok) {
       for (int small = 0; small < 2; ++small) {
         ctx->plan_small = small != 0;
         const BucketSched* t = tuned(ctx, sc.w, j);
-        want |= t ? t->P == 1 : j <= kLaneJMax;
+        // untuned buckets of any length may take the one-lane engine where
+        // its ring fits (the count decides later)
+        want |= t ? t->P == 1 : bucket_sched_ok(ctx, sc.w, j, 1, lane_default_R(j));
       }
       ctx->plan_small = false;
     }
@@ -334,7 +345,9 @@ void batched_flags(xt_ctx* ctx, const Score& sc, JFlags* jf, bool* lane_ok) {
     bucket_schedule(ctx, j, sc.w, &P, &R, &lg, &huge, true);
     ctx->forced_P = fP;
     keep.swap(ctx->tuning);
-    if (huge) jf->f[j] |= kJHuge;
+    // a bucket the group engine cannot hold runs on the one-lane engine when
+    // it can; only its WIDE pairs (group engine only) then go to the HUGE class
+    if (huge) jf->f[j] |= lane_ok[j] ? kJHugeWide : kJHuge;
   }
   ctx->plan_small = saved;
 }
@@ -373,7 +386,7 @@ void plan_counts(xt_ctx* ctx, const Score& sc, const int32_t (*cnt)[kNumJ], cons
         } else if (!ctx->forced_P) {
           const BucketSched* t = tuned(ctx, sc.w, jj);
           if (t) lane = t->P == 1;
-          else if (ctx->plan_small && jj >= 7) lane = false;  // latency rule below
+          else if (c < lane_min_pairs(jj)) lane = false;  // latency rule below
         }
       }
       if (lane) {
@@ -382,7 +395,7 @@ void plan_counts(xt_ctx* ctx, const Score& sc, const int32_t (*cnt)[kNumJ], cons
         int P = 0, R = 8, lg = 0;
         bool huge = false;
         const BucketSched* t = ctx->forced_P ? nullptr : tuned(ctx, sc.w, jj);
-        if (!ctx->forced_P && !t && ctx->plan_small && jj >= 7 && cls != CLS_WIDE) {
+        if (!ctx->forced_P && !t && c < lane_min_pairs(jj) && cls != CLS_WIDE) {
           // enough lanes per pair to fill the GPU, where the ring fits
           int want = 4;
           while (want < 32 && (int64_t)want * c < kLaneSlots) want *= 2;
@@ -395,12 +408,15 @@ void plan_counts(xt_ctx* ctx, const Score& sc, const int32_t (*cnt)[kNumJ], cons
           }
         }
         if (P == 0) bucket_schedule(ctx, jj, sc.w, &P, &R, &lg, &huge, true);
-        if (huge) {
-          // the flags gave this bucket no HUGE class, so its pairs would be lost
+        if (huge && cls != CLS_WIDE && lane_ok[jj]) {
+          lane_launch(ctx, sc, cls, jj, true, &L);  // no group ring fits: one lane per pair
+        } else if (huge) {
+          // the flags gave these pairs no HUGE class, so they would be lost
           pl->bad = true;
           continue;
+        } else {
+          L = queue_launch(ctx, cls, jj, P, R, lg);
         }
-        L = queue_launch(ctx, cls, jj, P, R, lg);
       }
       L.j_lo = j;
       L.j_hi = j;

@@ -67,7 +67,7 @@ __global__ void k_classify(const Batch* __restrict__ bd, Score sc, int32_t match
   // packed: the anchoring multiply and the 16-bit row keys (H * 64 + step) fit
   if (!wide && (jf & kJPacked) && ((bound + 1) << mshift) <= 32767 && bound * 64 + 63 <= 32767)
     cls = CLS_PACKED;
-  if (jf & kJHuge) cls = CLS_HUGE;
+  if ((jf & kJHuge) || (cls == CLS_WIDE && (jf & kJHugeWide))) cls = CLS_HUGE;
   w.pclass[k] = (uint8_t)cls;
   atomicAdd(&w.counts[(cls * kNumJ + j) * kNumSub + sub], 1);
 }

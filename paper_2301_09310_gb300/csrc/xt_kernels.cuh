@@ -18,6 +18,7 @@ constexpr int kNumClasses = 4;           // classes that need a DP kernel
 // per-bucket flags (Work::jflags)
 constexpr uint8_t kJHuge = 1;            // bucket's pairs go to the HUGE class
 constexpr uint8_t kJPacked = 2;          // bucket runs the one-lane engine: packed pairs allowed
+constexpr uint8_t kJHugeWide = 4;        // the bucket's WIDE pairs (group engine only) are HUGE
 constexpr int kJMin = 5;                 // length buckets j: qlen + 2 <= 2^j
 constexpr int kJMax = 21;
 constexpr int kNumJ = kJMax + 1;

@@ -499,11 +499,24 @@ xt_status xt_autotune(xt_ctx* ctx, const xt_scoring* sc, int j_max, double cells
     // may itself be a small call
     const double qmid = j == kJMin ? 16.0 : 0.75 * (1 << j);
     const double width = std::min<double>(2.0 * w + 1, qmid + std::min<double>(2.0 * w, 2.0 * qmid));
-    const double n_fill = 4.0 * ctx->num_sms * 4 * kLaneThreads;
-    const int n = (int)std::max(1024.0, std::min<double>({(double)(1 << 20), n_fill,
-                                                          cells_per_trial / (qmid * width)}));
+    const double wave = (double)ctx->num_sms * 4 * kLaneThreads;  // one pair per one-lane slot
+    int n = (int)std::max(1024.0, std::min<double>({(double)(1 << 20), 4.0 * wave,
+                                                    cells_per_trial / (qmid * width)}));
+    std::vector<BucketSched> big_cand = cand;
+    int big_reps = 3;
+    bool lane_cand = false;
+    for (auto& c : cand) lane_cand |= c.P == 1;
+    if (lane_cand && n < wave) {
+      // long pairs: below one wave the one-lane engine would be timed half
+      // idle, so time one full wave, with fewer candidates and one call each
+      n = (int)wave;
+      big_cand.clear();
+      for (auto& c : cand)
+        if ((c.P == 1 && c.R >= 8) || (c.P >= 16 && c.R == 8)) big_cand.push_back(c);
+      big_reps = 1;
+    }
     Trial big;
-    status = tune_bucket(ctx, sc, w, j, n, cand, /*small_only=*/false, 3, &big, &why);
+    status = tune_bucket(ctx, sc, w, j, n, big_cand, /*small_only=*/false, big_reps, &big, &why);
     if (status != XT_OK) break;
     {
       std::lock_guard<std::mutex> lk(ctx->mu);

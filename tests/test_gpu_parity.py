@@ -103,6 +103,13 @@ def test_huge_band_global_ring(ctx):
         qs.append(q)
         ts.append(np.concatenate([t, rng.integers(0, 4, 500)]))
         hs.append(30)
+    # and two of them again with a seed score that makes them WIDE: a bucket
+    # whose group ring does not fit runs its narrow pairs on one-lane strips
+    # and only its WIDE pairs on the global slabs
+    for k in (4, 5):
+        qs.append(qs[k])
+        ts.append(ts[k])
+        hs.append(40000)
     b = batch_from_lists(qs, ts, hs)
     import paper_2301_09310_gb300 as xt
     for sc in (ScoringParams(w=6000, zdrop=300), ScoringParams(w=1000, zdrop=300)):
