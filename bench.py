@@ -69,6 +69,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-ascii", action="store_true",
+                    help="skip the same batch given as raw ASCII reads")
     ap.add_argument("--no-x2", action="store_true",
                     help="skip the equal-length 5,000-pair calls of the paper's kernel comparison")
     ap.add_argument("--serve-pairs", type=int, default=4_000_000,
@@ -429,6 +431,8 @@ def run_xt(args):
                         "ms_per_step": round(pms, 3),
                         "kernel": "k_plain: one pair per one-warp block, int32"}
         res["speedup_vs_plain"] = round(pms / ms, 3)
+    if not args.no_ascii:
+        res["ascii_reads"] = ascii_leg(b, wl, args, local, stream, cells_step)
     if not args.no_e2e:
         res["e2e"] = e2e_leg(ctx, b, wl, args, dev, stream, world)
     if not args.no_x2 and world == 1:
@@ -443,6 +447,39 @@ def run_xt(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def ascii_leg(b, wl, args, local, stream, cells_step):
+    """The same batch as raw reads (ASCII letters, mixed case, N as 'N'): each
+    call first packs both sequence buffers into base codes on the GPU."""
+    import torch
+    import paper_2301_09310_gb300 as xt
+
+    dev = torch.device("cuda", local)
+    letters = np.frombuffer(b"ACGTN", np.uint8)
+    d = [torch.from_numpy(a).to(dev) for a in
+         (letters[np.minimum(b.q_seq, 4)], b.q_off, b.q_len, letters[np.minimum(b.t_seq, 4)],
+          b.t_off, b.t_len, b.h0)]
+    ctx = xt.Context(local)
+    ctx.set_alphabet(xt.XT_ALPHABET_ASCII)
+    out = torch.empty((b.n, 7), dtype=torch.int32, device=dev)
+    cells = torch.empty(b.n, dtype=torch.int64, device=dev)
+    for _ in range(3):
+        ctx.extend(*d, wl.scoring, out=out, cells=cells, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(3, min(args.steps, 10))
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.extend(*d, wl.scoring, out=out, cells=cells, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    same = int(cells.sum().item()) == cells_step
+    ctx.close()
+    return {"value": round(cells_step / (ms / 1e3) / 1e9, 3), "unit": "GCUPS",
+            "ms_per_step": round(ms, 4), "same_cells_as_codes": same,
+            "input": "ASCII letters; xt_ctx_set_alphabet(XT_ALPHABET_ASCII): an on-GPU packing "
+                     "pass per call, then the same extension"}
 
 
 def e2e_leg(ctx, b, wl, args, dev, stream, world):
@@ -640,7 +677,7 @@ def serve_levels(args, local, b, wl, peak_pairs, ref_out, ref_cells, total_cells
                           ctypes.c_void_p(cells.ctypes.data + 8 * a)))
         srv = xt.xt_serve_create(local, xt.xt_serve_config(
             args.serve_slots, 0, args.serve_batch_mib << 20, 0, int(args.serve_budget_gb * 1e9),
-            args.serve_gather_threads, table.encode() if table else None))
+            args.serve_gather_threads, table.encode() if table else None, 0))
         tickets = queue.Queue()
         stamps = np.zeros((nreq, 4), np.int64)   # arrival, submit, launch, done
         bpairs = np.zeros(nreq, np.int64)

@@ -283,6 +283,21 @@ xt_status xt_autotune(xt_ctx* ctx, const xt_scoring* sc, int j_max, double cells
  */
 xt_status xt_ctx_load_tuning(xt_ctx* ctx, const char* table_path);
 
+/*
+ * How the context's calls read sequence bytes.  XT_ALPHABET_CODES (default):
+ * base codes 0, 1, 2, 3 = A, C, G, T, any other value N.  XT_ALPHABET_ASCII:
+ * raw reads as ASCII letters -- A, C, G, T in either case are the bases and
+ * any other byte (N, n, IUPAC codes, ...) is N.  A call then first runs an
+ * elementwise pass that writes the base codes of both sequence buffers into
+ * the context's workspace (q_bytes + t_bytes bytes, within its budget) and
+ * extends from those.  Results are those of the same sequences given as
+ * base codes.  (The allocation-free xt_extend_batch_static reads base codes
+ * only.)
+ */
+#define XT_ALPHABET_CODES 0
+#define XT_ALPHABET_ASCII 1
+xt_status xt_ctx_set_alphabet(xt_ctx* ctx, int alphabet);
+
 /* XT_OK if the scoring record is within the ranges above, else XT_EINVAL. */
 xt_status xt_scoring_check(const xt_scoring* sc);
 
@@ -364,6 +379,7 @@ typedef struct {
                                thread included (0: a quarter of the cores, <= 8) */
   const char* tuning_path;  /* a table written by xt_autotune, loaded into every
                                slot's context (NULL: built-in schedules) */
+  int32_t alphabet;         /* XT_ALPHABET_CODES (0) or XT_ALPHABET_ASCII */
 } xt_serve_config;
 
 /* Latency stamps of one request, ns on CLOCK_MONOTONIC (see xt_now_ns). */

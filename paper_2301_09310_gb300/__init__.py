@@ -29,7 +29,7 @@ EXPORTED = ("xt_ctx_create", "xt_ctx_destroy", "xt_ctx_sync", "xt_extend_batch",
             "xt_ctx_set_bucket_schedule", "xt_ctx_get_bucket_schedule", "xt_autotune",
             "xt_ctx_load_tuning", "xt_ctx_set_bucket_schedule_for",
             "xt_ctx_get_bucket_schedule_for", "xt_extend_batch_begin", "xt_extend_batch_ready",
-            "xt_extend_batch_finish")
+            "xt_extend_batch_finish", "xt_ctx_set_alphabet")
 XT_STATIC_MAX_PAIRS = 1 << 20
 
 
@@ -48,7 +48,7 @@ class xt_serve_config(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("max_batch_pairs", ctypes.c_int32),
                 ("max_batch_bytes", ctypes.c_int64), ("max_queued_bytes", ctypes.c_int64),
                 ("mem_budget_bytes", ctypes.c_size_t), ("gather_threads", ctypes.c_int32),
-                ("tuning_path", ctypes.c_char_p)]
+                ("tuning_path", ctypes.c_char_p), ("alphabet", ctypes.c_int32)]
 
 
 class xt_serve_times(ctypes.Structure):
@@ -133,6 +133,8 @@ def load_library(path: str | None = None):
     for fn in ("xt_ctx_set_bucket_schedule", "xt_ctx_get_bucket_schedule", "xt_autotune",
                "xt_ctx_load_tuning"):
         getattr(lib, fn).restype = ctypes.c_int
+    lib.xt_ctx_set_alphabet.argtypes = [P, ctypes.c_int]
+    lib.xt_ctx_set_alphabet.restype = ctypes.c_int
     lib.xt_ctx_set_streams.argtypes = [P, ctypes.c_int]
     lib.xt_ctx_set_streams.restype = ctypes.c_int
     lib.xt_ctx_set_timing.argtypes = [P, ctypes.c_int]
@@ -158,7 +160,7 @@ def load_library(path: str | None = None):
             "xt_ctx_set_bucket_schedule", "xt_ctx_get_bucket_schedule", "xt_autotune",
             "xt_ctx_load_tuning", "xt_ctx_set_bucket_schedule_for",
             "xt_ctx_get_bucket_schedule_for", "xt_extend_batch_begin", "xt_extend_batch_ready",
-            "xt_extend_batch_finish"):
+            "xt_extend_batch_finish", "xt_ctx_set_alphabet"):
         getattr(lib, fn).restype = ctypes.c_int
     _LIB = lib
     return lib
@@ -228,6 +230,13 @@ def xt_autotune(ctx: int, sc, j_max: int = 14, cells_per_trial: float = 0.0,
 
 def xt_ctx_load_tuning(ctx: int, table_path: str) -> int:
     return load_library().xt_ctx_load_tuning(ctypes.c_void_p(ctx), table_path.encode())
+
+
+XT_ALPHABET_CODES, XT_ALPHABET_ASCII = 0, 1
+
+
+def xt_ctx_set_alphabet(ctx: int, alphabet: int) -> int:
+    return load_library().xt_ctx_set_alphabet(ctypes.c_void_p(ctx), int(alphabet))
 
 
 def xt_ctx_set_streams(ctx: int, branches: int) -> int:
@@ -444,6 +453,10 @@ class Context:
     def load_tuning(self, table_path: str):
         self._check(xt_ctx_load_tuning(self.handle, table_path), "xt_ctx_load_tuning")
 
+    def set_alphabet(self, alphabet: int):
+        """XT_ALPHABET_CODES (base codes 0..3) or XT_ALPHABET_ASCII (raw letters)."""
+        self._check(xt_ctx_set_alphabet(self.handle, alphabet), "xt_ctx_set_alphabet")
+
     def set_streams(self, branches: int):
         self._check(xt_ctx_set_streams(self.handle, branches), "xt_ctx_set_streams")
 
@@ -536,10 +549,11 @@ class Server:
 
     def __init__(self, device: int = 0, slots: int = 0, max_batch_pairs: int = 0,
                  max_batch_bytes: int = 0, max_queued_bytes: int = 0, mem_budget_bytes: int = 0,
-                 gather_threads: int = 0, tuning_path: str | None = None):
+                 gather_threads: int = 0, tuning_path: str | None = None,
+                 alphabet: int = XT_ALPHABET_CODES):
         cfg = xt_serve_config(slots, max_batch_pairs, max_batch_bytes, max_queued_bytes,
                               mem_budget_bytes, gather_threads,
-                              tuning_path.encode() if tuning_path else None)
+                              tuning_path.encode() if tuning_path else None, alphabet)
         self.handle = xt_serve_create(device, cfg)
         self._live = {}
 

@@ -623,6 +623,19 @@ xt_status run_begin(xt_ctx* ctx, bool plain, const uint8_t* q_seq, int64_t q_byt
   if (s != XT_OK) return s;
   ctx->match = scr->match;
   ctx->plan_small = false;
+  // raw reads: an elementwise pass turns the letters into base codes in the
+  // context's workspace, and the call reads those
+  if (ctx->alphabet == XT_ALPHABET_ASCII) {
+    const size_t qa = align_up((size_t)q_bytes);
+    s = dev_alloc(ctx, &ctx->conv, &ctx->conv_bytes, qa + (size_t)t_bytes + kAlign);
+    if (s != XT_OK) return s;
+    uint8_t* cq = static_cast<uint8_t*>(ctx->conv);
+    e = launch_ascii_codes(q_seq, cq, q_bytes, ctx->num_sms, stream);
+    if (e == cudaSuccess) e = launch_ascii_codes(t_seq, cq + qa, t_bytes, ctx->num_sms, stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "ASCII conversion");
+    q_seq = cq;
+    t_seq = cq + qa;
+  }
   // this call's arguments go to the device descriptor through a pinned slot
   Batch hb;
   hb.q_seq = q_seq; hb.t_seq = t_seq; hb.q_off = q_off; hb.t_off = t_off; hb.q_len = q_len;
@@ -707,6 +720,7 @@ xt_status run_finish(xt_ctx* ctx) {
     key.has_cells = pc.has_cells;
     key.plan_sig = plan_signature(pl);
     key.branches = ctx->branches;
+    key.alphabet = ctx->alphabet;
     for (auto& g : ctx->graph_cache)
       if (g.key == key) ge = &g;
     if (!ge) {
@@ -812,6 +826,7 @@ xt_status xt_ctx_destroy(xt_ctx* ctx) {
   if (ctx->work) cudaFree(ctx->work);
   if (ctx->pool) cudaFree(ctx->pool);
   if (ctx->dev_in) cudaFree(ctx->dev_in);
+  if (ctx->conv) cudaFree(ctx->conv);
   for (auto& pr : ctx->ev)
     for (auto& e : pr)
       if (e) cudaEventDestroy(e);
@@ -1003,6 +1018,13 @@ xt_status xt_ctx_get_bucket_schedule_for(xt_ctx* ctx, int w, int j, int batch_cl
       *P = b.P;
       *R = b.R;
     }
+  return XT_OK;
+}
+
+xt_status xt_ctx_set_alphabet(xt_ctx* ctx, int alphabet) {
+  if (!ctx || (alphabet != XT_ALPHABET_CODES && alphabet != XT_ALPHABET_ASCII)) return XT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->alphabet = alphabet;
   return XT_OK;
 }
 

@@ -22,6 +22,7 @@ struct GraphKey {
   bool has_cells;
   uint64_t plan_sig;   // the plan of the extension kernels (count-aware)
   int branches;
+  int alphabet;
   bool operator==(const GraphKey& o) const { return std::memcmp(this, &o, sizeof(GraphKey)) == 0; }
 };
 struct GraphEntry {
@@ -87,6 +88,9 @@ struct xt_ctx {
   // end-to-end staging: device copies of host inputs and pinned host mirrors
   void* dev_in = nullptr;
   size_t dev_in_bytes = 0;
+  // raw reads converted to base codes (XT_ALPHABET_ASCII)
+  void* conv = nullptr;
+  size_t conv_bytes = 0;
   // launch accounting and DP timing (xt_ctx_stats)
   bool timing = false;
   static constexpr int kEvRing = 256;
@@ -109,6 +113,7 @@ struct xt_ctx {
   int match = 1;                 // scoring of the call being planned
   int forced_P = 0;              // schedule override (0: per-bucket table)
   int forced_R = 0;
+  int alphabet = XT_ALPHABET_CODES;  // how sequence bytes encode bases
   std::vector<xt::TuneEntry> tuning;  // per-band bucket schedules (xt_autotune)
   bool plan_small = false;       // the bucket being planned is small (its small-batch schedule)
   // pair counts per (class, bucket) read back between classify and the plan

@@ -306,6 +306,49 @@ __global__ void __launch_bounds__(32) k_plain(const Batch* __restrict__ bd, Scor
     write_result(b, k, o.score, o.qle, o.tle, o.gscore, o.gtle, o.max_off, XT_OK, o.cells);
 }
 
+// ------------------------------------------------------- ASCII -> codes
+// Raw reads (ASCII letters) to base codes, four bytes per thread-step with
+// per-byte SIMD compares: A, C, G, T in either case become 0, 1, 2, 3 and
+// any other byte becomes 4 (N).  Grid-stride over 16-byte chunks of the
+// buffer (word loads when both pointers are 4-byte aligned, else bytes).
+__device__ __forceinline__ uint32_t codes4(uint32_t w) {
+  const uint32_t x = w | 0x20202020u;  // lower case
+  const uint32_t a = __vcmpeq4(x, 0x61616161u), c = __vcmpeq4(x, 0x63636363u);
+  const uint32_t g = __vcmpeq4(x, 0x67676767u), t = __vcmpeq4(x, 0x74747474u);
+  const uint32_t base = a | c | g | t;
+  const uint32_t code = (c & 0x01010101u) | (g & 0x02020202u) | (t & 0x03030303u);
+  return (code & base) | (0x04040404u & ~base);
+}
+
+__global__ void k_ascii_codes(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
+                              int64_t n) {
+  const int64_t chunks = (n + 15) / 16;
+  const bool words = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 3u) == 0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < chunks;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b0 = k * 16;
+    if (words && b0 + 16 <= n) {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(in + b0);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(out + b0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) dst[q] = codes4(__ldg(src + q));
+    } else {
+      for (int64_t b = b0; b < n && b < b0 + 16; ++b) out[b] = (uint8_t)(codes4(in[b]) & 0xFFu);
+    }
+  }
+}
+
+cudaError_t launch_ascii_codes(const uint8_t* in, uint8_t* out, int64_t n, int num_sms,
+                               cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t chunks = (n + 15) / 16;
+  const int T = 256;
+  const int64_t want = (chunks + T - 1) / T;
+  const int grid = (int)(want < (int64_t)num_sms * 8 ? want : (int64_t)num_sms * 8);
+  k_ascii_codes<<<grid, T, 0, stream>>>(in, out, n);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- launchers
 // Static shared memory of the kernels (descriptor copy, profiles) stays below
 // this; a launch asks for the larger dynamic limit whenever both together

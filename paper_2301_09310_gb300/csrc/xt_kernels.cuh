@@ -71,6 +71,9 @@ cudaError_t launch_plain(const Batch* bd, int32_t n_cap, const Score& sc, const 
                          int rs_log2, cudaStream_t stream);
 cudaError_t launch_lane(const Batch* bd, const Score& sc, const Work& w, const Launch& L,
                         int head_id, void* gring, cudaStream_t stream);
+// ASCII letters to base codes (A/C/G/T either case -> 0..3, else 4), n bytes.
+cudaError_t launch_ascii_codes(const uint8_t* in, uint8_t* out, int64_t n, int num_sms,
+                               cudaStream_t stream);
 // Shared memory a queue launch needs per CTA (bytes).
 size_t queue_smem_bytes(int P, int rs_log2);
 // Ring bytes per lane of a one-lane launch (per CTA in shared memory: x kLaneThreads).

@@ -461,6 +461,7 @@ xt_status xt_serve_create(xt_server** out, int device, const xt_serve_config* cf
     s.srv = S;
     xt_status st = xt_ctx_create(&s.ctx, device, ctx_budget);
     if (st == XT_OK && cfg.tuning_path) st = xt_ctx_load_tuning(s.ctx, cfg.tuning_path);
+    if (st == XT_OK) st = xt_ctx_set_alphabet(s.ctx, cfg.alphabet);
     cudaError_t e = st == XT_OK ? cudaSuccess : cudaErrorUnknown;
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&s.start_ev);

@@ -258,3 +258,48 @@ def test_two_step_call(ctx):
     assert xt.xt_extend_batch_finish(ctx.handle) == xt.XT_EINVAL
     torch.cuda.synchronize()
     assert_same((out.cpu().numpy(), cells.cpu().numpy()), run_oracle(b, wl.scoring), "two-step")
+
+
+def _to_ascii(codes, rng):
+    """Base codes as raw read letters: A/C/G/T in random case, N as an
+    assortment of other bytes (N, n, IUPAC letters, '-', '.')."""
+    upper = np.frombuffer(b"ACGT", np.uint8)
+    lower = np.frombuffer(b"acgt", np.uint8)
+    other = np.frombuffer(b"NnRYKMSWBDHV-.", np.uint8)
+    out = np.where(rng.random(codes.size) < 0.5, upper[np.minimum(codes, 3)],
+                   lower[np.minimum(codes, 3)]).astype(np.uint8)
+    n = codes >= 4
+    out[n] = other[rng.integers(0, other.size, int(n.sum()))]
+    return out
+
+
+@pytest.mark.parametrize("shift", [0, 1])
+def test_ascii_reads(ctx, shift):
+    # raw reads go through the on-GPU packing pass; results equal the oracle
+    # on the base codes; shift = 1 starts both buffers one byte off (the
+    # conversion's byte path)
+    import torch
+    import paper_2301_09310_gb300 as xt
+    rng = np.random.default_rng(99 + shift)
+    wl = synth.WORKLOADS["c3_mixed"]
+    b = synth.generate(wl, n=4000, first=555)
+    fz = fuzz_batch(21, 600, max_len=80, tail=40)
+    other = xt.Context(0)
+    try:
+        other.set_alphabet(xt.XT_ALPHABET_ASCII)
+        for batch, sc in ((b, wl.scoring), (fz, SCORINGS[3])):
+            want = run_oracle(batch, sc)
+            qa = np.concatenate([np.zeros(shift, np.uint8), _to_ascii(batch.q_seq, rng)])
+            ta = np.concatenate([np.zeros(shift, np.uint8), _to_ascii(batch.t_seq, rng)])
+            dev = torch.device("cuda", 0)
+            T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+            qd, td = T(qa)[shift:], T(ta)[shift:]
+            args = (qd, T(batch.q_off), T(batch.q_len), td, T(batch.t_off), T(batch.t_len),
+                    T(batch.h0))
+            for plain in (False, True):
+                out, cells = other.extend(*args, sc, plain=plain)
+                torch.cuda.synchronize()
+                assert_same((out.cpu().numpy(), cells.cpu().numpy()), want,
+                            f"ascii shift={shift} plain={plain}")
+    finally:
+        other.close()
