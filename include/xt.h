@@ -151,6 +151,31 @@ xt_status xt_extend_batch_ready(xt_ctx* ctx, int* ready);
 xt_status xt_extend_batch_finish(xt_ctx* ctx);
 
 /*
+ * Both-direction extension of seeds (Sec. II-A: seed-and-extend grows each
+ * exact-match seed to both sides).  Pair k holds a query and a target window
+ * (as in xt_extend_batch) and a seed: seed_len[k] matching bases at query
+ * position q_beg[k] and target position t_beg[k], with score h0[k].  The left
+ * side extends the reversed prefixes (query [0, q_beg), target [0, t_beg))
+ * from h0; the right side extends the suffixes (query [q_beg + seed_len,
+ * qlen), target [t_beg + seed_len, tlen)) from the left side's local best
+ * (h0 when the left side is empty).  left[k] and right[k] are xt_results of
+ * each side, positions counted from the seed outwards; left_cells /
+ * right_cells (NULL: not written) their useful cells.  A seed outside its
+ * pair (or a pair outside its buffers) gives XT_EINVAL on both sides.  All
+ * arrays are device memory; q_beg, t_beg, seed_len int32[n_pairs].  The
+ * call reads the sizes of the reversed prefixes back before it copies them
+ * into the context's workspace (the two sides' sequences: at most the
+ * seeds' prefix lengths summed), then enqueues both sides on `stream`.
+ */
+xt_status xt_extend_seeds(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_bytes, const int64_t* q_off,
+                          const int32_t* q_len, const uint8_t* t_seq, int64_t t_bytes,
+                          const int64_t* t_off, const int32_t* t_len, const int32_t* q_beg,
+                          const int32_t* t_beg, const int32_t* seed_len, const int32_t* h0,
+                          int32_t n_pairs, const xt_scoring* sc, xt_result* left,
+                          xt_result* right, int64_t* left_cells, int64_t* right_cells,
+                          void* stream);
+
+/*
  * Plain extension: one pair per thread block (one warp), 32-bit arithmetic,
  * no bucketing and no persistent queue -- the comparison kernel.  Same
  * arguments, conventions and results as xt_extend_batch.

@@ -29,7 +29,7 @@ EXPORTED = ("xt_ctx_create", "xt_ctx_destroy", "xt_ctx_sync", "xt_extend_batch",
             "xt_ctx_set_bucket_schedule", "xt_ctx_get_bucket_schedule", "xt_autotune",
             "xt_ctx_load_tuning", "xt_ctx_set_bucket_schedule_for",
             "xt_ctx_get_bucket_schedule_for", "xt_extend_batch_begin", "xt_extend_batch_ready",
-            "xt_extend_batch_finish", "xt_ctx_set_alphabet")
+            "xt_extend_batch_finish", "xt_ctx_set_alphabet", "xt_extend_seeds")
 XT_STATIC_MAX_PAIRS = 1 << 20
 
 
@@ -133,6 +133,9 @@ def load_library(path: str | None = None):
     for fn in ("xt_ctx_set_bucket_schedule", "xt_ctx_get_bucket_schedule", "xt_autotune",
                "xt_ctx_load_tuning"):
         getattr(lib, fn).restype = ctypes.c_int
+    lib.xt_extend_seeds.argtypes = [P, P, I64, P, P, P, I64, P, P, P, P, P, P, I32,
+                                    ctypes.POINTER(xt_scoring), P, P, P, P, P]
+    lib.xt_extend_seeds.restype = ctypes.c_int
     lib.xt_ctx_set_alphabet.argtypes = [P, ctypes.c_int]
     lib.xt_ctx_set_alphabet.restype = ctypes.c_int
     lib.xt_ctx_set_streams.argtypes = [P, ctypes.c_int]
@@ -160,7 +163,7 @@ def load_library(path: str | None = None):
             "xt_ctx_set_bucket_schedule", "xt_ctx_get_bucket_schedule", "xt_autotune",
             "xt_ctx_load_tuning", "xt_ctx_set_bucket_schedule_for",
             "xt_ctx_get_bucket_schedule_for", "xt_extend_batch_begin", "xt_extend_batch_ready",
-            "xt_extend_batch_finish", "xt_ctx_set_alphabet"):
+            "xt_extend_batch_finish", "xt_ctx_set_alphabet", "xt_extend_seeds"):
         getattr(lib, fn).restype = ctypes.c_int
     _LIB = lib
     return lib
@@ -350,6 +353,16 @@ def xt_extend_batch_host(ctx, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_of
                  t_len, h0, n, sc, out, cells, stream)
 
 
+def xt_extend_seeds(ctx, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off, t_len, q_beg, t_beg,
+                    seed_len, h0, n, sc, left, right, left_cells, right_cells, stream) -> int:
+    """Both-direction extension of seeds; raw device pointers as in include/xt.h."""
+    V = ctypes.c_void_p
+    return load_library().xt_extend_seeds(
+        V(ctx), V(q_seq), int(q_bytes), V(q_off), V(q_len), V(t_seq), int(t_bytes), V(t_off),
+        V(t_len), V(q_beg), V(t_beg), V(seed_len), V(h0), int(n), ctypes.byref(_scoring(sc)),
+        V(left), V(right), V(left_cells), V(right_cells), V(stream))
+
+
 def xt_extend_batch_begin(ctx, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off, t_len, h0, n,
                           sc, out, cells, stream) -> int:
     return _call("xt_extend_batch_begin", ctx, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes,
@@ -514,6 +527,39 @@ class Context:
                   cells.data_ptr() if cells is not None else 0, stream.cuda_stream)
         self._check(s, fn)
         return out, cells
+
+    def extend_seeds(self, q_seq, q_off, q_len, t_seq, t_off, t_len, q_beg, t_beg, seed_len, h0,
+                     scoring, stream=None):
+        """Both-direction extension of seeds (xt_extend_seeds): CUDA tensors in,
+        (left [n, 7], right [n, 7], left_cells [n], right_cells [n]) out."""
+        import torch
+        d = self._dev
+        q_seq = d(q_seq, torch.uint8, "q_seq")
+        t_seq = d(t_seq, torch.uint8, "t_seq")
+        q_off = d(q_off, torch.int64, "q_off")
+        t_off = d(t_off, torch.int64, "t_off")
+        arrs32 = [d(a, torch.int32, nm) for a, nm in ((q_len, "q_len"), (t_len, "t_len"),
+                                                      (q_beg, "q_beg"), (t_beg, "t_beg"),
+                                                      (seed_len, "seed_len"), (h0, "h0"))]
+        q_len, t_len, q_beg, t_beg, seed_len, h0 = arrs32
+        n = int(q_len.numel())
+        dev = q_len.device
+        left = torch.empty((n, 7), dtype=torch.int32, device=dev)
+        right = torch.empty((n, 7), dtype=torch.int32, device=dev)
+        lc = torch.empty(n, dtype=torch.int64, device=dev)
+        rc = torch.empty(n, dtype=torch.int64, device=dev)
+        if stream is None:
+            stream = torch.cuda.current_stream(dev)
+        V = ctypes.c_void_p
+        s = load_library().xt_extend_seeds(
+            V(self.handle), V(q_seq.data_ptr()), q_seq.numel(), V(q_off.data_ptr()),
+            V(q_len.data_ptr()), V(t_seq.data_ptr()), t_seq.numel(), V(t_off.data_ptr()),
+            V(t_len.data_ptr()), V(q_beg.data_ptr()), V(t_beg.data_ptr()),
+            V(seed_len.data_ptr()), V(h0.data_ptr()), n, ctypes.byref(_scoring(scoring)),
+            V(left.data_ptr()), V(right.data_ptr()), V(lc.data_ptr()), V(rc.data_ptr()),
+            V(stream.cuda_stream))
+        self._check(s, "xt_extend_seeds")
+        return left, right, lc, rc
 
     def extend_host(self, q_seq, q_off, q_len, t_seq, t_off, t_len, h0, scoring, out=None,
                     cells=None, stream=None):

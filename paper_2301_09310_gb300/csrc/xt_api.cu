@@ -827,6 +827,8 @@ xt_status xt_ctx_destroy(xt_ctx* ctx) {
   if (ctx->pool) cudaFree(ctx->pool);
   if (ctx->dev_in) cudaFree(ctx->dev_in);
   if (ctx->conv) cudaFree(ctx->conv);
+  if (ctx->seed_ws) cudaFree(ctx->seed_ws);
+  if (ctx->seed_rev) cudaFree(ctx->seed_rev);
   for (auto& pr : ctx->ev)
     for (auto& e : pr)
       if (e) cudaEventDestroy(e);
@@ -910,6 +912,78 @@ xt_status xt_extend_batch_plain(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_byt
   std::lock_guard<std::mutex> lk(ctx->mu);
   return run(ctx, true, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off, t_len, h0, n_pairs,
              sc, out, cells_out, (cudaStream_t)stream);
+}
+
+xt_status xt_extend_seeds(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_bytes, const int64_t* q_off,
+                          const int32_t* q_len, const uint8_t* t_seq, int64_t t_bytes,
+                          const int64_t* t_off, const int32_t* t_len, const int32_t* q_beg,
+                          const int32_t* t_beg, const int32_t* seed_len, const int32_t* h0,
+                          int32_t n_pairs, const xt_scoring* sc, xt_result* left,
+                          xt_result* right, int64_t* left_cells, int64_t* right_cells,
+                          void* stream) {
+  if (!ctx) return XT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  xt_status s = check_args(ctx, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off, t_len, h0,
+                           n_pairs, sc, left);
+  if (s != XT_OK) return s;
+  if (n_pairs > 0 && (!q_beg || !t_beg || !seed_len || !right))
+    return fail(ctx, XT_EINVAL, "null array");
+  if (n_pairs == 0) return XT_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, XT_ECUDA, "cudaSetDevice");
+  // workspace: per-seed arrays and the block sums
+  const size_t n = (size_t)n_pairs;
+  const size_t nb = (n + 1023) / 1024;
+  size_t off = 0;
+  const size_t o_lql = off; off = align_up(off + 4 * n);
+  const size_t o_ltl = off; off = align_up(off + 4 * n);
+  const size_t o_lqo = off; off = align_up(off + 8 * n);
+  const size_t o_lto = off; off = align_up(off + 8 * n);
+  const size_t o_rql = off; off = align_up(off + 4 * n);
+  const size_t o_rtl = off; off = align_up(off + 4 * n);
+  const size_t o_rqo = off; off = align_up(off + 8 * n);
+  const size_t o_rto = off; off = align_up(off + 8 * n);
+  const size_t o_rh0 = off; off = align_up(off + 4 * n);
+  const size_t o_bq = off; off = align_up(off + 8 * nb);
+  const size_t o_bt = off; off = align_up(off + 8 * nb);
+  const size_t o_tot = off; off = align_up(off + 16);
+  s = dev_alloc(ctx, &ctx->seed_ws, &ctx->seed_ws_bytes, off);
+  if (s != XT_OK) return s;
+  char* d = static_cast<char*>(ctx->seed_ws);
+  SeedWork sw;
+  sw.lq_len = (int32_t*)(d + o_lql); sw.lt_len = (int32_t*)(d + o_ltl);
+  sw.lq_off = (int64_t*)(d + o_lqo); sw.lt_off = (int64_t*)(d + o_lto);
+  sw.rq_len = (int32_t*)(d + o_rql); sw.rt_len = (int32_t*)(d + o_rtl);
+  sw.rq_off = (int64_t*)(d + o_rqo); sw.rt_off = (int64_t*)(d + o_rto);
+  sw.rh0 = (int32_t*)(d + o_rh0);
+  sw.block_q = (int64_t*)(d + o_bq); sw.block_t = (int64_t*)(d + o_bt);
+  sw.totals = (int64_t*)(d + o_tot);
+  sw.rev_q = sw.rev_t = nullptr;
+  // lengths and the prefix sums up to their totals, which size the copies
+  cudaError_t e = launch_seed_front(n_pairs, q_len, t_len, q_off, t_off, q_bytes, t_bytes, q_beg,
+                                    t_beg, seed_len, sw, st);
+  int64_t* tot_host = reinterpret_cast<int64_t*>(ctx->seg_host + 512);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tot_host, sw.totals, 16, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->seg_ev, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(ctx->seg_ev);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "seed layout");
+  const int64_t tq = tot_host[0], tt = tot_host[1];
+  const size_t qa = align_up((size_t)tq);
+  s = dev_alloc(ctx, &ctx->seed_rev, &ctx->seed_rev_bytes, qa + align_up((size_t)tt) + kAlign);
+  if (s != XT_OK) return s;
+  sw.rev_q = static_cast<uint8_t*>(ctx->seed_rev);
+  sw.rev_t = sw.rev_q + qa;
+  e = launch_seed_reverse(n_pairs, q_seq, q_off, t_seq, t_off, sw, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "seed prefixes");
+  // left: the reversed prefixes from the seed's score
+  s = run(ctx, false, sw.rev_q, tq, sw.lq_off, sw.lq_len, sw.rev_t, tt, sw.lt_off, sw.lt_len, h0,
+          n_pairs, sc, left, left_cells, st);
+  if (s != XT_OK) return s;
+  // right: the suffixes from the left side's best
+  e = launch_seed_right_h0(n_pairs, h0, left, sw, st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "seed right scores");
+  return run(ctx, false, q_seq, q_bytes, sw.rq_off, sw.rq_len, t_seq, t_bytes, sw.rt_off,
+             sw.rt_len, sw.rh0, n_pairs, sc, right, right_cells, st);
 }
 
 xt_status xt_extend_batch_host(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_bytes,

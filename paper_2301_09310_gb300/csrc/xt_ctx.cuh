@@ -91,6 +91,11 @@ struct xt_ctx {
   // raw reads converted to base codes (XT_ALPHABET_ASCII)
   void* conv = nullptr;
   size_t conv_bytes = 0;
+  // both-direction seed extension: per-seed arrays, reversed prefixes
+  void* seed_ws = nullptr;
+  size_t seed_ws_bytes = 0;
+  void* seed_rev = nullptr;
+  size_t seed_rev_bytes = 0;
   // launch accounting and DP timing (xt_ctx_stats)
   bool timing = false;
   static constexpr int kEvRing = 256;

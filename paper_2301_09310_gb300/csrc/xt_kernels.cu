@@ -349,6 +349,157 @@ cudaError_t launch_ascii_codes(const uint8_t* in, uint8_t* out, int64_t n, int n
   return cudaGetLastError();
 }
 
+// ------------------------------------------------ both-direction seeds
+// Seed k: an exact match of seed_len[k] bases at query q_beg[k] and target
+// t_beg[k].  Left lengths are the prefixes before the seed, right views the
+// suffixes after it (offsets into the caller's buffers); a seed outside its
+// pair gets length -1 on both sides, which classify reports as XT_EINVAL.
+__global__ void k_seed_prep(int32_t n, const int32_t* __restrict__ q_len,
+                            const int32_t* __restrict__ t_len, const int64_t* __restrict__ q_off,
+                            const int64_t* __restrict__ t_off, int64_t q_bytes, int64_t t_bytes,
+                            const int32_t* __restrict__ q_beg, const int32_t* __restrict__ t_beg,
+                            const int32_t* __restrict__ seed_len, SeedWork sw) {
+  const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int32_t ql = q_len[k], tl = t_len[k], qb = q_beg[k], tb = t_beg[k], sl = seed_len[k];
+  const int64_t qo = q_off[k], to = t_off[k];
+  // the pair inside its buffers (the reversed copy reads them before classify
+  // checks anything), the seed inside the pair
+  const bool ok = ql >= 0 && tl >= 0 && ql <= XT_MAX_LEN && tl <= XT_MAX_LEN && qo >= 0 &&
+                  to >= 0 && qo <= q_bytes - ql && to <= t_bytes - tl && qb >= 0 && tb >= 0 &&
+                  sl >= 0 && (int64_t)qb + sl <= ql && (int64_t)tb + sl <= tl;
+  sw.lq_len[k] = ok ? qb : -1;
+  sw.lt_len[k] = ok ? tb : -1;
+  sw.rq_len[k] = ok ? ql - qb - sl : -1;
+  sw.rt_len[k] = ok ? tl - tb - sl : -1;
+  sw.rq_off[k] = ok ? qo + qb + sl : 0;
+  sw.rt_off[k] = ok ? to + tb + sl : 0;
+}
+
+// Exclusive prefix sums of the left lengths (both sides at once), in blocks
+// of kSeedScanBlock pairs: block-local sums first, then a scan of the block
+// totals, then the final offsets.
+constexpr int kSeedScanBlock = 1024;
+
+__device__ __forceinline__ void block_scan2(int64_t& a, int64_t& b, int64_t* s_a, int64_t* s_b) {
+  // inclusive block-wide scan of two values (blockDim.x = kSeedScanBlock)
+  const int t = threadIdx.x;
+  s_a[t] = a;
+  s_b[t] = b;
+  __syncthreads();
+  for (int d = 1; d < kSeedScanBlock; d <<= 1) {
+    const int64_t va = t >= d ? s_a[t - d] : 0, vb = t >= d ? s_b[t - d] : 0;
+    __syncthreads();
+    s_a[t] += va;
+    s_b[t] += vb;
+    __syncthreads();
+  }
+  a = s_a[t];
+  b = s_b[t];
+}
+
+__global__ void __launch_bounds__(kSeedScanBlock) k_seed_sums(int32_t n, SeedWork sw) {
+  __shared__ int64_t s_a[kSeedScanBlock], s_b[kSeedScanBlock];
+  const int32_t k = blockIdx.x * kSeedScanBlock + threadIdx.x;
+  int64_t a = k < n ? max(sw.lq_len[k], 0) : 0, b = k < n ? max(sw.lt_len[k], 0) : 0;
+  block_scan2(a, b, s_a, s_b);
+  if (threadIdx.x == kSeedScanBlock - 1) {
+    sw.block_q[blockIdx.x] = a;
+    sw.block_t[blockIdx.x] = b;
+  }
+}
+
+// One block: exclusive scan of the block totals (in place) and the grand totals.
+__global__ void __launch_bounds__(kSeedScanBlock) k_seed_block_scan(int32_t nblocks, SeedWork sw) {
+  __shared__ int64_t s_a[kSeedScanBlock], s_b[kSeedScanBlock];
+  int64_t carry_a = 0, carry_b = 0;
+  for (int32_t base = 0; base < nblocks; base += kSeedScanBlock) {
+    const int32_t i = base + threadIdx.x;
+    const int64_t a0 = i < nblocks ? sw.block_q[i] : 0, b0 = i < nblocks ? sw.block_t[i] : 0;
+    int64_t a = a0, b = b0;
+    block_scan2(a, b, s_a, s_b);
+    if (i < nblocks) {
+      sw.block_q[i] = carry_a + a - a0;
+      sw.block_t[i] = carry_b + b - b0;
+    }
+    carry_a += s_a[kSeedScanBlock - 1];
+    carry_b += s_b[kSeedScanBlock - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    sw.totals[0] = carry_a;
+    sw.totals[1] = carry_b;
+  }
+}
+
+__global__ void __launch_bounds__(kSeedScanBlock) k_seed_offsets(int32_t n, SeedWork sw) {
+  __shared__ int64_t s_a[kSeedScanBlock], s_b[kSeedScanBlock];
+  const int32_t k = blockIdx.x * kSeedScanBlock + threadIdx.x;
+  const int64_t a0 = k < n ? max(sw.lq_len[k], 0) : 0, b0 = k < n ? max(sw.lt_len[k], 0) : 0;
+  int64_t a = a0, b = b0;
+  block_scan2(a, b, s_a, s_b);
+  if (k < n) {
+    sw.lq_off[k] = sw.block_q[blockIdx.x] + a - a0;
+    sw.lt_off[k] = sw.block_t[blockIdx.x] + b - b0;
+  }
+}
+
+// The reversed prefixes, one warp per seed.
+__global__ void k_seed_reverse(int32_t n, const uint8_t* __restrict__ q_seq,
+                               const int64_t* __restrict__ q_off,
+                               const uint8_t* __restrict__ t_seq,
+                               const int64_t* __restrict__ t_off, SeedWork sw) {
+  const int32_t k = (int32_t)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (k >= n) return;
+  const int32_t lq = sw.lq_len[k], lt = sw.lt_len[k];
+  const uint8_t* q = q_seq + q_off[k];
+  const uint8_t* t = t_seq + t_off[k];
+  for (int32_t i = lane; i < lq; i += 32) sw.rev_q[sw.lq_off[k] + i] = q[lq - 1 - i];
+  for (int32_t i = lane; i < lt; i += 32) sw.rev_t[sw.lt_off[k] + i] = t[lt - 1 - i];
+}
+
+// Right side's seed score: the left side's local best (the seed's own
+// score where the left side had nothing to extend).
+__global__ void k_seed_right_h0(int32_t n, const int32_t* __restrict__ h0,
+                                const xt_result* __restrict__ left, SeedWork sw) {
+  const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  sw.rh0[k] = left[k].status == XT_OK ? left[k].score : h0[k];
+}
+
+cudaError_t launch_seed_front(int32_t n, const int32_t* q_len, const int32_t* t_len,
+                              const int64_t* q_off, const int64_t* t_off, int64_t q_bytes,
+                              int64_t t_bytes, const int32_t* q_beg, const int32_t* t_beg,
+                              const int32_t* seed_len, const SeedWork& sw, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  k_seed_prep<<<(n + 255) / 256, 256, 0, stream>>>(n, q_len, t_len, q_off, t_off, q_bytes, t_bytes,
+                                                  q_beg, t_beg, seed_len, sw);
+  const int32_t nb = (n + kSeedScanBlock - 1) / kSeedScanBlock;
+  k_seed_sums<<<nb, kSeedScanBlock, 0, stream>>>(n, sw);
+  k_seed_block_scan<<<1, kSeedScanBlock, 0, stream>>>(nb, sw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seed_reverse(int32_t n, const uint8_t* q_seq, const int64_t* q_off,
+                                const uint8_t* t_seq, const int64_t* t_off, const SeedWork& sw,
+                                cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  const int32_t nb = (n + kSeedScanBlock - 1) / kSeedScanBlock;
+  k_seed_offsets<<<nb, kSeedScanBlock, 0, stream>>>(n, sw);
+  const int64_t threads = (int64_t)n * 32;
+  k_seed_reverse<<<(int)((threads + 255) / 256), 256, 0, stream>>>(n, q_seq, q_off, t_seq, t_off,
+                                                                  sw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seed_right_h0(int32_t n, const int32_t* h0, const xt_result* left,
+                                 const SeedWork& sw, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  k_seed_right_h0<<<(n + 255) / 256, 256, 0, stream>>>(n, h0, left, sw);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- launchers
 // Static shared memory of the kernels (descriptor copy, profiles) stays below
 // this; a launch asks for the larger dynamic limit whenever both together

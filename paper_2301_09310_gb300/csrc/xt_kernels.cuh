@@ -74,6 +74,29 @@ cudaError_t launch_lane(const Batch* bd, const Score& sc, const Work& w, const L
 // ASCII letters to base codes (A/C/G/T either case -> 0..3, else 4), n bytes.
 cudaError_t launch_ascii_codes(const uint8_t* in, uint8_t* out, int64_t n, int num_sms,
                                cudaStream_t stream);
+// Both-direction extension of seeds: device workspace (carved by the host).
+struct SeedWork {
+  int32_t *lq_len, *lt_len;   // left (reversed prefix) lengths, -1: invalid seed
+  int64_t *lq_off, *lt_off;   // their offsets in rev_q / rev_t
+  int32_t *rq_len, *rt_len;   // right (suffix) lengths, -1: invalid seed
+  int64_t *rq_off, *rt_off;   // their offsets in the caller's buffers
+  int32_t* rh0;               // right side's seed score
+  int64_t *block_q, *block_t; // per-block sums of the left lengths
+  int64_t* totals;            // [2]: bytes of rev_q and rev_t
+  uint8_t *rev_q, *rev_t;     // reversed prefixes
+};
+// Prep, lengths, and the scan up to the totals (sw.totals, read by the host).
+cudaError_t launch_seed_front(int32_t n, const int32_t* q_len, const int32_t* t_len,
+                              const int64_t* q_off, const int64_t* t_off, int64_t q_bytes,
+                              int64_t t_bytes, const int32_t* q_beg, const int32_t* t_beg,
+                              const int32_t* seed_len, const SeedWork& sw, cudaStream_t stream);
+// Offsets of the reversed prefixes and the reversed copies (sw.rev_q/rev_t set).
+cudaError_t launch_seed_reverse(int32_t n, const uint8_t* q_seq, const int64_t* q_off,
+                                const uint8_t* t_seq, const int64_t* t_off, const SeedWork& sw,
+                                cudaStream_t stream);
+// Right side's seed scores from the left results.
+cudaError_t launch_seed_right_h0(int32_t n, const int32_t* h0, const xt_result* left,
+                                 const SeedWork& sw, cudaStream_t stream);
 // Shared memory a queue launch needs per CTA (bytes).
 size_t queue_smem_bytes(int P, int rs_log2);
 // Ring bytes per lane of a one-lane launch (per CTA in shared memory: x kLaneThreads).
