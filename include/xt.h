@@ -326,6 +326,63 @@ xt_status xt_ctx_set_alphabet(xt_ctx* ctx, int alphabet);
 /* XT_OK if the scoring record is within the ranges above, else XT_EINVAL. */
 xt_status xt_scoring_check(const xt_scoring* sc);
 
+/*
+ * BWA-MEM-compatible extension (opt-in; the default definition above is
+ * Eq. 1 of Sec. II-A as read there).  Seed-and-extend aligners that take
+ * their seeds from BWA-MEM (the seeds of the paper's real-data runs,
+ * Sec. V) extend with a variant of Eq. 1; this call computes that variant,
+ * stated here in full (rows i = target, columns j = query):
+ *
+ *   gaps open from the match value, so an insertion never touches a deletion:
+ *     M(i,j) = H(i-1,j-1) + S(i,j) if H(i-1,j-1) > 0, else 0 (may be < 0)
+ *     E(i,j) = max(0, M(i,j-1) - o_ins - e_ins, E(i,j-1) - e_ins)   insertion
+ *     F(i,j) = max(0, M(i-1,j) - o_del - e_del, F(i-1,j) - e_del)   deletion
+ *     H(i,j) = max(M, E, F); cells a row does not compute hold 0, and E is 0
+ *     at a row's first computed column;
+ *   boundaries: H(-1,-1) = h0; row -1 is the insertion run from the seed,
+ *     max(0, h0 - o_ins - e_ins*(c+1)) inside the band (no deletion opens from
+ *     it); column -1 the deletion run max(0, h0 - o_del - e_del*(r+1)), used
+ *     only as the diagonal source of (r+1, 0) when row r computed column 0
+ *     (no insertion opens from it);
+ *   band narrowing: with gain = qlen*match + end_bonus, w_x = 1 if gain < o_x,
+ *     else (gain - o_x) / e_x + 1 (x = ins, del), and the band is |i - j| <=
+ *     min(w, w_ins, w_del) =: w';
+ *   row trimming: row 0 computes [0, min(qlen, w'+1)); if [a, b] is the
+ *     maximal run of computed columns of row i with H > 0 that holds the row's
+ *     best column mj (the largest column of the row maximum m), row i+1
+ *     computes [max(a, i+1-w'), min(b+2, i+w'+2, qlen));
+ *   after each row, in order: if the row computed column qlen-1 and H(i,
+ *     qlen-1) >= gscore, gscore = that value and gtle = i+1 (the latest row
+ *     wins ties; gscore starts at -1); the extension stops if m = 0; a new
+ *     local best needs m > best (as in the default definition); otherwise,
+ *     with zdrop > 0, di = i - bi, dj = mj - bj, it stops after the row when
+ *     best - m - (di - dj)*e_del > zdrop (di > dj) or best - m - (dj - di)*
+ *     e_ins > zdrop (otherwise).
+ *
+ * Results and cells_out are as for xt_extend_batch: cells_out counts the
+ * computed columns of every row with m > 0 that was evaluated.  Degenerate
+ * pairs give the default definition's results.  Per-pair errors are those of
+ * xt_extend_batch plus rows wider than XT_BWA_MAX_WIDTH columns
+ * (min(qlen, 2w'+1) > XT_BWA_MAX_WIDTH: status XT_EINVAL).  The scoring
+ * record: match in [1, 127]; mismatch and n_score in [-127, 0]; o_del and
+ * o_ins in [0, 1023]; e_del and e_ins in [1, 1023]; w >= 0; end_bonus in
+ * [0, 2^20]; zdrop <= 0 disables the z-drop.  Asynchronous on `stream`; the
+ * context's alphabet applies.  Inputs, outputs and ownership as for
+ * xt_extend_batch; the call does not use CUDA graphs or bucket schedules.
+ */
+typedef struct {
+  int32_t match, mismatch, n_score;
+  int32_t o_del, e_del, o_ins, e_ins;
+  int32_t w, zdrop, end_bonus;
+} xt_bwa_scoring;
+#define XT_BWA_MAX_WIDTH 8192
+xt_status xt_bwa_scoring_check(const xt_bwa_scoring* sc);
+xt_status xt_extend_batch_bwa(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_bytes,
+                              const int64_t* q_off, const int32_t* q_len, const uint8_t* t_seq,
+                              int64_t t_bytes, const int64_t* t_off, const int32_t* t_len,
+                              const int32_t* h0, int32_t n_pairs, const xt_bwa_scoring* sc,
+                              xt_result* out, int64_t* cells_out, void* stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* xt_status_str(xt_status s);
 

@@ -29,13 +29,23 @@ EXPORTED = ("xt_ctx_create", "xt_ctx_destroy", "xt_ctx_sync", "xt_extend_batch",
             "xt_ctx_set_bucket_schedule", "xt_ctx_get_bucket_schedule", "xt_autotune",
             "xt_ctx_load_tuning", "xt_ctx_set_bucket_schedule_for",
             "xt_ctx_get_bucket_schedule_for", "xt_extend_batch_begin", "xt_extend_batch_ready",
-            "xt_extend_batch_finish", "xt_ctx_set_alphabet", "xt_extend_seeds")
+            "xt_extend_batch_finish", "xt_ctx_set_alphabet", "xt_extend_seeds",
+            "xt_extend_batch_bwa", "xt_bwa_scoring_check")
 XT_STATIC_MAX_PAIRS = 1 << 20
 
 
 class xt_scoring(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in
                 ("match", "mismatch", "gap_open", "gap_extend", "w", "zdrop", "n_score")]
+
+
+class xt_bwa_scoring(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in
+                ("match", "mismatch", "n_score", "o_del", "e_del", "o_ins", "e_ins", "w", "zdrop",
+                 "end_bonus")]
+
+
+XT_BWA_MAX_WIDTH = 8192
 
 
 class xt_stats(ctypes.Structure):
@@ -136,6 +146,10 @@ def load_library(path: str | None = None):
     lib.xt_extend_seeds.argtypes = [P, P, I64, P, P, P, I64, P, P, P, P, P, P, I32,
                                     ctypes.POINTER(xt_scoring), P, P, P, P, P]
     lib.xt_extend_seeds.restype = ctypes.c_int
+    lib.xt_extend_batch_bwa.argtypes = batch_args[:11] + [ctypes.POINTER(xt_bwa_scoring), P, P, P]
+    lib.xt_extend_batch_bwa.restype = ctypes.c_int
+    lib.xt_bwa_scoring_check.argtypes = [ctypes.POINTER(xt_bwa_scoring)]
+    lib.xt_bwa_scoring_check.restype = ctypes.c_int
     lib.xt_ctx_set_alphabet.argtypes = [P, ctypes.c_int]
     lib.xt_ctx_set_alphabet.restype = ctypes.c_int
     lib.xt_ctx_set_streams.argtypes = [P, ctypes.c_int]
@@ -363,6 +377,27 @@ def xt_extend_seeds(ctx, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off, t_
         V(left), V(right), V(left_cells), V(right_cells), V(stream))
 
 
+def _bwa_scoring(sc) -> xt_bwa_scoring:
+    if isinstance(sc, xt_bwa_scoring):
+        return sc
+    if hasattr(sc, "as_tuple"):
+        return xt_bwa_scoring(*sc.as_tuple())
+    return xt_bwa_scoring(*sc)
+
+
+def xt_bwa_scoring_check(sc) -> int:
+    return load_library().xt_bwa_scoring_check(ctypes.byref(_bwa_scoring(sc)))
+
+
+def xt_extend_batch_bwa(ctx, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off, t_len, h0, n,
+                        sc, out, cells, stream) -> int:
+    """BWA-MEM-compatible extension; raw device pointers as in include/xt.h."""
+    V = ctypes.c_void_p
+    return load_library().xt_extend_batch_bwa(
+        V(ctx), V(q_seq), int(q_bytes), V(q_off), V(q_len), V(t_seq), int(t_bytes), V(t_off),
+        V(t_len), V(h0), int(n), ctypes.byref(_bwa_scoring(sc)), V(out), V(cells), V(stream))
+
+
 def xt_extend_batch_begin(ctx, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off, t_len, h0, n,
                           sc, out, cells, stream) -> int:
     return _call("xt_extend_batch_begin", ctx, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes,
@@ -526,6 +561,40 @@ class Context:
                   t_len.data_ptr(), h0.data_ptr(), n, _scoring(scoring), out.data_ptr(),
                   cells.data_ptr() if cells is not None else 0, stream.cuda_stream)
         self._check(s, fn)
+        return out, cells
+
+    def extend_bwa(self, q_seq, q_off, q_len, t_seq, t_off, t_len, h0, scoring, out=None,
+                   cells=None, want_cells=True, stream=None):
+        """BWA-MEM-compatible extension (xt_extend_batch_bwa): the arguments of
+        extend(); scoring is an xt_bwa_scoring, a BwaScoringParams or a tuple
+        (match, mismatch, n_score, o_del, e_del, o_ins, e_ins, w, zdrop,
+        end_bonus)."""
+        import torch
+        d = self._dev
+        q_seq = d(q_seq, torch.uint8, "q_seq")
+        t_seq = d(t_seq, torch.uint8, "t_seq")
+        q_off = d(q_off, torch.int64, "q_off")
+        t_off = d(t_off, torch.int64, "t_off")
+        q_len = d(q_len, torch.int32, "q_len")
+        t_len = d(t_len, torch.int32, "t_len")
+        h0 = d(h0, torch.int32, "h0")
+        n = int(q_len.numel())
+        for name, t in (("q_off", q_off), ("t_off", t_off), ("t_len", t_len), ("h0", h0)):
+            if t.numel() != n:
+                raise ValueError(f"{name} has {t.numel()} entries, expected {n}")
+        dev = q_len.device
+        if out is None:
+            out = torch.empty((n, 7), dtype=torch.int32, device=dev)
+        if cells is None and want_cells:
+            cells = torch.empty(n, dtype=torch.int64, device=dev)
+        if stream is None:
+            stream = torch.cuda.current_stream(dev)
+        s = xt_extend_batch_bwa(self.handle, q_seq.data_ptr(), q_seq.numel(), q_off.data_ptr(),
+                                q_len.data_ptr(), t_seq.data_ptr(), t_seq.numel(),
+                                t_off.data_ptr(), t_len.data_ptr(), h0.data_ptr(), n, scoring,
+                                out.data_ptr(), cells.data_ptr() if cells is not None else 0,
+                                stream.cuda_stream)
+        self._check(s, "xt_extend_batch_bwa")
         return out, cells
 
     def extend_seeds(self, q_seq, q_off, q_len, t_seq, t_off, t_len, q_beg, t_beg, seed_len, h0,

@@ -91,6 +91,31 @@ xt_status dev_alloc(xt_ctx* ctx, void** p, size_t* have, size_t want) {
 
 }  // namespace
 
+xt_status xt::ctx_fail(xt_ctx* ctx, xt_status s, const char* msg) { return fail(ctx, s, msg); }
+
+xt_status xt::ctx_cuda_fail(xt_ctx* ctx, cudaError_t e, const char* where) {
+  return cuda_fail(ctx, e, where);
+}
+
+xt_status xt::ctx_alloc(xt_ctx* ctx, void** p, size_t* have, size_t want) {
+  return dev_alloc(ctx, p, have, want);
+}
+
+xt_status xt::ctx_codes(xt_ctx* ctx, const uint8_t** q_seq, int64_t q_bytes,
+                        const uint8_t** t_seq, int64_t t_bytes, cudaStream_t stream) {
+  if (ctx->alphabet != XT_ALPHABET_ASCII) return XT_OK;
+  const size_t qa = align_up((size_t)q_bytes);
+  xt_status s = dev_alloc(ctx, &ctx->conv, &ctx->conv_bytes, qa + (size_t)t_bytes + kAlign);
+  if (s != XT_OK) return s;
+  uint8_t* cq = static_cast<uint8_t*>(ctx->conv);
+  cudaError_t e = launch_ascii_codes(*q_seq, cq, q_bytes, ctx->num_sms, stream);
+  if (e == cudaSuccess) e = launch_ascii_codes(*t_seq, cq + qa, t_bytes, ctx->num_sms, stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "ASCII conversion");
+  *q_seq = cq;
+  *t_seq = cq + qa;
+  return XT_OK;
+}
+
 void xt::drop_graphs(xt_ctx* ctx) {
   for (auto& g : ctx->graph_cache)
     if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -307,7 +332,8 @@ constexpr int32_t kLaneSlots = 77824;    // one-lane thread slots of a full GPU 
 // time on one lane grows with its length, so a bucket of long queries needs
 // close to a full wave of pairs before the one-lane engine pays; short ones
 // finish fast even when a bucket leaves most lanes idle.
-inline int32_t lane_min_pairs(int j) { return j >= 10 ? 32768 : (j >= 7 ? kBucketSmall : 0); }
+constexpr int kLongJ = 10;               // buckets of queries longer than 510 bases
+inline int32_t lane_min_pairs(int j) { return j >= kLongJ ? 32768 : (j >= 7 ? kBucketSmall : 0); }
 
 // Flags for classify: kJHuge where the default group ring does not fit
 // (band geometry only), kJPacked where a one-lane schedule is possible for
@@ -370,6 +396,15 @@ void plan_counts(xt_ctx* ctx, const Score& sc, const int32_t (*cnt)[kNumJ], cons
                  const bool* lane_ok, Plan* pl) {
   pl->jf = jf;
   const bool saved = ctx->plan_small;
+  // long queries: one lane per pair needs many pairs to fill the GPU, but
+  // the long buckets of one call run side by side, so when together they
+  // hold two full waves of lanes each of them takes the one-lane engine
+  int64_t long_pairs = 0;
+  for (int cls = CLS_PACKED; cls <= CLS_NARROW; ++cls)
+    for (int j = kLongJ; j < kNumJ; ++j)
+      if (lane_ok[j]) long_pairs += cnt[cls][j];
+  const bool long_lanes = long_pairs >= 2 * (int64_t)kLaneSlots;
+  auto min_pairs = [&](int jj) { return jj >= kLongJ && long_lanes ? 0 : lane_min_pairs(jj); };
   for (int cls = CLS_PACKED; cls <= CLS_WIDE; ++cls) {
     int prev = -1;
     for (int j = kJMax; j >= 0; --j) {
@@ -386,7 +421,7 @@ void plan_counts(xt_ctx* ctx, const Score& sc, const int32_t (*cnt)[kNumJ], cons
         } else if (!ctx->forced_P) {
           const BucketSched* t = tuned(ctx, sc.w, jj);
           if (t) lane = t->P == 1;
-          else if (c < lane_min_pairs(jj)) lane = false;  // latency rule below
+          else if (c < min_pairs(jj)) lane = false;  // latency rule below
         }
       }
       if (lane) {
@@ -395,7 +430,7 @@ void plan_counts(xt_ctx* ctx, const Score& sc, const int32_t (*cnt)[kNumJ], cons
         int P = 0, R = 8, lg = 0;
         bool huge = false;
         const BucketSched* t = ctx->forced_P ? nullptr : tuned(ctx, sc.w, jj);
-        if (!ctx->forced_P && !t && c < lane_min_pairs(jj) && cls != CLS_WIDE) {
+        if (!ctx->forced_P && !t && c < min_pairs(jj) && cls != CLS_WIDE) {
           // enough lanes per pair to fill the GPU, where the ring fits
           int want = 4;
           while (want < 32 && (int64_t)want * c < kLaneSlots) want *= 2;
@@ -625,17 +660,8 @@ xt_status run_begin(xt_ctx* ctx, bool plain, const uint8_t* q_seq, int64_t q_byt
   ctx->plan_small = false;
   // raw reads: an elementwise pass turns the letters into base codes in the
   // context's workspace, and the call reads those
-  if (ctx->alphabet == XT_ALPHABET_ASCII) {
-    const size_t qa = align_up((size_t)q_bytes);
-    s = dev_alloc(ctx, &ctx->conv, &ctx->conv_bytes, qa + (size_t)t_bytes + kAlign);
-    if (s != XT_OK) return s;
-    uint8_t* cq = static_cast<uint8_t*>(ctx->conv);
-    e = launch_ascii_codes(q_seq, cq, q_bytes, ctx->num_sms, stream);
-    if (e == cudaSuccess) e = launch_ascii_codes(t_seq, cq + qa, t_bytes, ctx->num_sms, stream);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "ASCII conversion");
-    q_seq = cq;
-    t_seq = cq + qa;
-  }
+  s = ctx_codes(ctx, &q_seq, q_bytes, &t_seq, t_bytes, stream);
+  if (s != XT_OK) return s;
   // this call's arguments go to the device descriptor through a pinned slot
   Batch hb;
   hb.q_seq = q_seq; hb.t_seq = t_seq; hb.q_off = q_off; hb.t_off = t_off; hb.q_len = q_len;
@@ -829,6 +855,7 @@ xt_status xt_ctx_destroy(xt_ctx* ctx) {
   if (ctx->conv) cudaFree(ctx->conv);
   if (ctx->seed_ws) cudaFree(ctx->seed_ws);
   if (ctx->seed_rev) cudaFree(ctx->seed_rev);
+  if (ctx->bwa_ws) cudaFree(ctx->bwa_ws);
   for (auto& pr : ctx->ev)
     for (auto& e : pr)
       if (e) cudaEventDestroy(e);

@@ -53,6 +53,15 @@ struct TuneEntry {
 bool bucket_sched_ok(const struct ::xt_ctx* ctx, int w, int j, int P, int R);
 // Drop every captured graph of the context.
 void drop_graphs(struct ::xt_ctx* ctx);
+// Record an error message on the context and return s (or XT_ECUDA for e).
+xt_status ctx_fail(struct ::xt_ctx* ctx, xt_status s, const char* msg);
+xt_status ctx_cuda_fail(struct ::xt_ctx* ctx, cudaError_t e, const char* where);
+// Grow *p (holding *have bytes) to at least `want` bytes within the budget.
+xt_status ctx_alloc(struct ::xt_ctx* ctx, void** p, size_t* have, size_t want);
+// With the ASCII alphabet, convert both sequence buffers to base codes in the
+// context's workspace and point *q_seq / *t_seq at them (no-op otherwise).
+xt_status ctx_codes(struct ::xt_ctx* ctx, const uint8_t** q_seq, int64_t q_bytes,
+                    const uint8_t** t_seq, int64_t t_bytes, cudaStream_t stream);
 
 // A call between its classify pass and its extension kernels.
 struct PendingCall {
@@ -96,6 +105,10 @@ struct xt_ctx {
   size_t seed_ws_bytes = 0;
   void* seed_rev = nullptr;
   size_t seed_rev_bytes = 0;
+  // BWA-MEM-compatible calls: class bytes, order, counters
+  void* bwa_ws = nullptr;
+  size_t bwa_ws_bytes = 0;
+  int bwa_blocks[8] = {};        // resident CTAs per SM of each group-size kernel (0: unknown)
   // launch accounting and DP timing (xt_ctx_stats)
   bool timing = false;
   static constexpr int kEvRing = 256;

@@ -56,6 +56,32 @@ class ScoringParams:
 
 
 @dataclass(frozen=True)
+class BwaScoringParams:
+    """Scoring of the BWA-MEM-compatible extension (same field meaning as the
+    C ABI's xt_bwa_scoring)."""
+    match: int = 1
+    mismatch: int = -4
+    n_score: int = -1
+    o_del: int = 6
+    e_del: int = 1
+    o_ins: int = 6
+    e_ins: int = 1
+    w: int = 100
+    zdrop: int = 100
+    end_bonus: int = 5
+
+    def as_tuple(self):
+        return (self.match, self.mismatch, self.n_score, self.o_del, self.e_del, self.o_ins,
+                self.e_ins, self.w, self.zdrop, self.end_bonus)
+
+    @staticmethod
+    def from_scoring(sc: "ScoringParams", end_bonus: int = 5) -> "BwaScoringParams":
+        """The same penalties for insertions and deletions as a default scoring."""
+        return BwaScoringParams(sc.match, sc.mismatch, sc.n_score, sc.gap_open, sc.gap_extend,
+                                sc.gap_open, sc.gap_extend, sc.w, sc.zdrop, end_bonus)
+
+
+@dataclass(frozen=True)
 class Workload:
     name: str
     n_pairs: int
