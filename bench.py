@@ -39,6 +39,8 @@ METRIC = "seed-extension GCUPS & extensions/s (bit-exact), batched vs plain; p50
 # Integer-ALU issue peak: 152 SMs x 128 int32 lanes per SM per clock (measured
 # issue-bound rate of IADD/IMNMX/PRMT/DPX ops on this GPU) x 2070 MHz max SM clock.
 SMS, LANES, MAX_MHZ = 152, 128, 2070.0
+# BWA-MEM-compatible cell, 32-bit: S, M (add, select), F and E (add-max each), H (3-way max), row key
+BWA_OPS_PER_CELL = 10
 # Algorithmic instructions per cell with the fused DPX forms native on sm_103a:
 # S (byte permute), anchored diagonal (multiply + add-min), E and F (add-max
 # with relu each), H (3-way max), H - alpha, row key (multiply-add + max): 9-10
@@ -514,9 +516,14 @@ def bwa_leg(b, wl, args, local, stream):
     ms = e0.elapsed_time(e1) / reps
     n_cells = int(cells.sum().item())
     ctx.close()
+    achieved = n_cells * BWA_OPS_PER_CELL / (ms / 1e3) / 1e12
+    peak = SMS * LANES * MAX_MHZ * 1e6 / 1e12
     return {"value": round(n_cells / (ms / 1e3) / 1e9, 3), "unit": "GCUPS",
             "ms_per_step": round(ms, 4), "useful_cells": n_cells,
             "ext_per_s": round(b.n / (ms / 1e3), 1),
+            "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
+                         "unit": "Tops/s (int-ALU instructions)", "frac": round(achieved / peak, 4),
+                         "ops_per_cell": BWA_OPS_PER_CELL},
             "scoring": list(sc.as_tuple()),
             "kernel": "k_bwa: one pair per group of 4..512 lanes, a row at a time, int32"}
 
