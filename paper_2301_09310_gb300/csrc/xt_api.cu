@@ -662,20 +662,15 @@ xt_status run_begin(xt_ctx* ctx, bool plain, const uint8_t* q_seq, int64_t q_byt
   // context's workspace, and the call reads those
   s = ctx_codes(ctx, &q_seq, q_bytes, &t_seq, t_bytes, stream);
   if (s != XT_OK) return s;
-  // this call's arguments go to the device descriptor through a pinned slot
+  // this call's arguments go to the device descriptor through a one-thread
+  // kernel (a kernel parameter, not a copy: a host-to-device copy here would
+  // queue behind bulk copies of other streams)
   Batch hb;
   hb.q_seq = q_seq; hb.t_seq = t_seq; hb.q_off = q_off; hb.t_off = t_off; hb.q_len = q_len;
   hb.t_len = t_len; hb.h0 = h0; hb.q_bytes = q_bytes; hb.t_bytes = t_bytes; hb.n = n;
   hb.out = out; hb.cells = cells;
-  const int slot = ctx->desc_next;
-  ctx->desc_next = (slot + 1) % kDescSlots;
-  e = cudaEventSynchronize(ctx->desc_ev[slot]);  // that slot's previous copy has run
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "descriptor slot");
-  ctx->desc_host[slot] = hb;
-  e = cudaMemcpyAsync(pc.desc, &ctx->desc_host[slot], sizeof(Batch), cudaMemcpyHostToDevice,
-                      stream);
-  if (e == cudaSuccess) e = cudaEventRecord(ctx->desc_ev[slot], stream);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "descriptor copy");
+  e = launch_store_desc(pc.desc, hb, stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "descriptor");
   if (!plain) {
     // classify and order with count-independent bucket flags, then bring the
     // pair count of every (class, bucket) back for the plan
@@ -788,7 +783,7 @@ xt_status run_finish(xt_ctx* ctx) {
     if (e != cudaSuccess) return cuda_fail(ctx, e, ("launch " + ctx->launch_error).c_str());
   }
   ctx->calls += 1;
-  ctx->launches += 3 + dp;  // classify, scan, scatter + DP kernels
+  ctx->launches += 4 + dp;  // descriptor, classify, scan, scatter + DP kernels
   ctx->dp_launches += dp;
   return XT_OK;
 }
@@ -824,10 +819,7 @@ xt_status xt_ctx_create(xt_ctx** out, int device, size_t mem_budget_bytes) {
   c->budget = mem_budget_bytes;
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
   c->smem_optin = max_smem_per_block_optin(device);
-  bool ok = cudaHostAlloc((void**)&c->desc_host, sizeof(Batch) * kDescSlots,
-                          cudaHostAllocDefault) == cudaSuccess;
-  for (int k = 0; ok && k < kDescSlots; ++k)
-    ok = cudaEventCreateWithFlags(&c->desc_ev[k], cudaEventDisableTiming) == cudaSuccess;
+  bool ok = true;
   ok = ok && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
   ok = ok && cudaHostAlloc((void**)&c->seg_host, 4096, cudaHostAllocDefault) == cudaSuccess;
   ok = ok && cudaEventCreateWithFlags(&c->seg_ev, cudaEventDisableTiming) == cudaSuccess;
@@ -836,6 +828,9 @@ xt_status xt_ctx_create(xt_ctx** out, int device, size_t mem_budget_bytes) {
     ok = cudaStreamCreateWithFlags(&c->aux[b], cudaStreamNonBlocking) == cudaSuccess &&
          cudaEventCreateWithFlags(&c->join_ev[b], cudaEventDisableTiming) == cudaSuccess;
   }
+  ok = ok && cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) == cudaSuccess;
+  for (auto& ev : c->stage_ev)
+    ok = ok && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     xt_ctx_destroy(c);
@@ -860,13 +855,13 @@ xt_status xt_ctx_destroy(xt_ctx* ctx) {
     for (auto& e : pr)
       if (e) cudaEventDestroy(e);
   drop_graphs(ctx);
-  for (auto& e : ctx->desc_ev)
-    if (e) cudaEventDestroy(e);
-  if (ctx->desc_host) cudaFreeHost(ctx->desc_host);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->seg_host) cudaFreeHost(ctx->seg_host);
   if (ctx->seg_ev) cudaEventDestroy(ctx->seg_ev);
   if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  for (auto& ev : ctx->stage_ev)
+    if (ev) cudaEventDestroy(ev);
   for (int b = 0; b < kMaxBranches; ++b) {
     if (ctx->aux[b]) cudaStreamDestroy(ctx->aux[b]);
     if (ctx->join_ev[b]) cudaEventDestroy(ctx->join_ev[b]);
@@ -1037,31 +1032,111 @@ xt_status xt_extend_batch_host(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_byte
   const size_t o_h0 = off; off = align_up(off + 4 * n);
   const size_t o_out = off; off = align_up(off + sizeof(xt_result) * n);
   const size_t o_cells = off; off = align_up(off + 8 * n);
+  const size_t o_ends = off; off = align_up(off + 16 * kMaxChunks);
   s = dev_alloc(ctx, &ctx->dev_in, &ctx->dev_in_bytes, off);
   if (s != XT_OK) return s;
   char* d = (char*)ctx->dev_in;
+  const int64_t* dqo = (const int64_t*)(d + o_qo);
+  const int64_t* dto = (const int64_t*)(d + o_to);
+  const int32_t* dql = (const int32_t*)(d + o_ql);
+  const int32_t* dtl = (const int32_t*)(d + o_tl);
+  const int32_t* dh0 = (const int32_t*)(d + o_h0);
+  xt_result* dout = (xt_result*)(d + o_out);
+  int64_t* dcells = cells_out ? (int64_t*)(d + o_cells) : nullptr;
+  unsigned long long* dends = (unsigned long long*)(d + o_ends);
   cudaError_t e = cudaSuccess;
-  auto h2d = [&](size_t o, const void* src, size_t bytes) {
-    if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(d + o, src, bytes, cudaMemcpyHostToDevice, st);
+  auto h2d = [&](size_t o, const void* src, size_t bytes, cudaStream_t on) {
+    if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(d + o, src, bytes, cudaMemcpyHostToDevice, on);
   };
-  h2d(o_q, q_seq, (size_t)q_bytes);
-  h2d(o_t, t_seq, (size_t)t_bytes);
-  h2d(o_qo, q_off, 8 * n);
-  h2d(o_to, t_off, 8 * n);
-  h2d(o_ql, q_len, 4 * n);
-  h2d(o_tl, t_len, 4 * n);
-  h2d(o_h0, h0, 4 * n);
+  // many pairs: chunks of at least kChunkPairs pairs, each extended as soon as
+  // the sequence bytes it reads are on the device, while the copy stream
+  // brings the next chunk's bytes and takes the finished chunks' results back
+  const int chunks = ctx->alphabet != XT_ALPHABET_CODES
+                         ? 1
+                         : (int)std::min<int64_t>(kMaxChunks, (int64_t)n_pairs / kChunkPairs);
+  if (chunks <= 1) {
+    h2d(o_q, q_seq, (size_t)q_bytes, st);
+    h2d(o_t, t_seq, (size_t)t_bytes, st);
+    h2d(o_qo, q_off, 8 * n, st);
+    h2d(o_to, t_off, 8 * n, st);
+    h2d(o_ql, q_len, 4 * n, st);
+    h2d(o_tl, t_len, 4 * n, st);
+    h2d(o_h0, h0, 4 * n, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "host to device copy");
+    s = run(ctx, false, (const uint8_t*)(d + o_q), q_bytes, dqo, dql, (const uint8_t*)(d + o_t),
+            t_bytes, dto, dtl, dh0, n_pairs, sc, dout, dcells, st);
+    if (s != XT_OK) return s;
+    e = cudaMemcpyAsync(out, dout, sizeof(xt_result) * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && cells_out)
+      e = cudaMemcpyAsync(cells_out, dcells, 8 * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "device to host copy");
+    return XT_OK;
+  }
+  cudaStream_t cs = ctx->copy_stream;
+  cudaEvent_t* ev = ctx->stage_ev;  // [0]: start, [1]: metadata, [2+k]: chunk k's bytes,
+                                    // [2+chunks+k]: chunk k extended
+  const int32_t cp = (int32_t)((((int64_t)n_pairs + chunks - 1) / chunks + 255) / 256 * 256);
+  e = cudaEventRecord(ev[0], st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[0], 0);
+  h2d(o_qo, q_off, 8 * n, cs);
+  h2d(o_to, t_off, 8 * n, cs);
+  h2d(o_ql, q_len, 4 * n, cs);
+  h2d(o_tl, t_len, 4 * n, cs);
+  h2d(o_h0, h0, 4 * n, cs);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[1], cs);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev[1], 0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dends, 0, 16 * kMaxChunks, st);
+  if (e == cudaSuccess)
+    e = launch_chunk_ends(dqo, dql, dto, dtl, n_pairs, cp, q_bytes, t_bytes, dends, st);
+  unsigned long long* ends = reinterpret_cast<unsigned long long*>(ctx->seg_host + 768);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ends, dends, 16 * kMaxChunks, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->seg_ev, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(ctx->seg_ev);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "chunk layout");
+  // chunk k needs every byte below the furthest end of chunks 0..k
+  int64_t need_q[kMaxChunks], need_t[kMaxChunks];
+  for (int k = 0; k < chunks; ++k) {
+    need_q[k] = std::max<int64_t>(k ? need_q[k - 1] : 0, (int64_t)ends[2 * k]);
+    need_t[k] = std::max<int64_t>(k ? need_t[k - 1] : 0, (int64_t)ends[2 * k + 1]);
+  }
+  for (int k = 0; k < chunks && e == cudaSuccess; ++k) {
+    const int64_t q0 = k ? need_q[k - 1] : 0, t0 = k ? need_t[k - 1] : 0;
+    h2d(o_q + (size_t)q0, q_seq + q0, (size_t)(need_q[k] - q0), cs);
+    h2d(o_t + (size_t)t0, t_seq + t0, (size_t)(need_t[k] - t0), cs);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2 + k], cs);
+  }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "host to device copy");
-  s = run(ctx, false, (const uint8_t*)(d + o_q), q_bytes, (const int64_t*)(d + o_qo),
-          (const int32_t*)(d + o_ql), (const uint8_t*)(d + o_t), t_bytes,
-          (const int64_t*)(d + o_to), (const int32_t*)(d + o_tl), (const int32_t*)(d + o_h0),
-          n_pairs, sc, (xt_result*)(d + o_out), cells_out ? (int64_t*)(d + o_cells) : nullptr, st);
-  if (s != XT_OK) return s;
-  e = cudaMemcpyAsync(out, d + o_out, sizeof(xt_result) * n, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess && cells_out)
-    e = cudaMemcpyAsync(cells_out, d + o_cells, 8 * n, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "device to host copy");
+  for (int k = 0; k < chunks; ++k) {
+    const int32_t p0 = (int32_t)std::min<int64_t>((int64_t)k * cp, n_pairs);
+    const int32_t p1 = (int32_t)std::min<int64_t>((int64_t)(k + 1) * cp, n_pairs);
+    if (p1 <= p0) continue;
+    e = cudaStreamWaitEvent(st, ev[2 + k], 0);
+    if (e != cudaSuccess) break;
+    s = run(ctx, false, (const uint8_t*)(d + o_q), q_bytes, dqo + p0, dql + p0,
+            (const uint8_t*)(d + o_t), t_bytes, dto + p0, dtl + p0, dh0 + p0, p1 - p0, sc,
+            dout + p0, dcells ? dcells + p0 : nullptr, st);
+    if (s != XT_OK) {
+      cudaStreamSynchronize(cs);
+      cudaStreamSynchronize(st);
+      return s;
+    }
+    e = cudaEventRecord(ev[2 + chunks + k], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[2 + chunks + k], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(out + p0, dout + p0, sizeof(xt_result) * (size_t)(p1 - p0),
+                          cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess && cells_out)
+      e = cudaMemcpyAsync(cells_out + p0, dcells + p0, 8 * (size_t)(p1 - p0),
+                          cudaMemcpyDeviceToHost, cs);
+    if (e != cudaSuccess) break;
+  }
+  cudaError_t e2 = cudaStreamSynchronize(cs);
+  if (e == cudaSuccess) e = e2;
+  e2 = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "chunked host call");
   return XT_OK;
 }
 

@@ -30,7 +30,6 @@ struct GraphEntry {
   int seen = 0;                   // calls with this key (captured on the second)
   cudaGraphExec_t exec = nullptr;
 };
-constexpr int kDescSlots = 64;   // pinned staging slots for the per-call descriptor
 constexpr int kMaxBranches = 8;  // streams the DP launches of one call fork onto
 
 // Schedule of one length bucket: P lanes per pair (1: the one-lane engine),
@@ -62,6 +61,20 @@ xt_status ctx_alloc(struct ::xt_ctx* ctx, void** p, size_t* have, size_t want);
 // context's workspace and point *q_seq / *t_seq at them (no-op otherwise).
 xt_status ctx_codes(struct ::xt_ctx* ctx, const uint8_t** q_seq, int64_t q_bytes,
                     const uint8_t** t_seq, int64_t t_bytes, cudaStream_t stream);
+
+// Host-buffer calls of many pairs run in chunks of pairs whose sequence
+// bytes are copied while earlier chunks extend (xt_extend_batch_host).
+constexpr int kMaxChunks = 8;
+constexpr int32_t kChunkPairs = 1 << 20;   // pairs per chunk at least (a chunk fills the GPU)
+// ends[2k], ends[2k+1]: how far chunk k's pairs read into the query and the
+// target buffer (see xt_stage.cu); ends must be zeroed first.
+// Store a call's batch descriptor into device memory (one thread; the
+// descriptor travels as a kernel parameter).
+cudaError_t launch_store_desc(Batch* dst, const Batch& b, cudaStream_t stream);
+cudaError_t launch_chunk_ends(const int64_t* q_off, const int32_t* q_len, const int64_t* t_off,
+                              const int32_t* t_len, int32_t n, int32_t chunk_pairs,
+                              int64_t q_bytes, int64_t t_bytes, unsigned long long* ends,
+                              cudaStream_t stream);
 
 // A call between its classify pass and its extension kernels.
 struct PendingCall {
@@ -109,6 +122,9 @@ struct xt_ctx {
   void* bwa_ws = nullptr;
   size_t bwa_ws_bytes = 0;
   int bwa_blocks[8] = {};        // resident CTAs per SM of each group-size kernel (0: unknown)
+  // host-buffer calls: a copy stream and its events (chunked staging)
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t stage_ev[2 * xt::kMaxChunks + 2] = {};
   // launch accounting and DP timing (xt_ctx_stats)
   bool timing = false;
   static constexpr int kEvRing = 256;
@@ -116,9 +132,7 @@ struct xt_ctx {
   int ev_pending = 0;
   int calls = 0, launches = 0, dp_launches = 0;
   // per-call batch descriptor: pinned host slots copied to a device slot
-  xt::Batch* desc_host = nullptr;
-  cudaEvent_t desc_ev[xt::kDescSlots] = {};
-  int desc_next = 0;
+
   // CUDA graphs of whole calls
   bool graphs = true;
   cudaStream_t cap_stream = nullptr;

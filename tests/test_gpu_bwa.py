@@ -77,6 +77,18 @@ def test_every_group_size(ctx, L, n):
         assert_same(run_gpu_bwa(ctx, b, sc), run_oracle_bwa(b, sc), f"L={L} {sc}")
 
 
+def test_large_scores_and_row_widths(ctx):
+    # seed scores past 16 bits, and rows of 209..256 columns (16-lane groups)
+    wl = synth.WORKLOADS["c3_mixed"]
+    b = synth.generate(wl, n=6000, first=31)
+    sc = BwaScoringParams.from_scoring(wl.scoring)
+    big = synth.Batch(b.q_seq, b.q_off, b.q_len, b.t_seq, b.t_off, b.t_len, b.h0 + 16400)
+    assert_same(run_gpu_bwa(ctx, big, sc), run_oracle_bwa(big, sc), "large h0")
+    b2 = synth.generate(synth.x2_workload(250, n_pairs=40))
+    sc2 = BwaScoringParams(w=250, zdrop=0)
+    assert_same(run_gpu_bwa(ctx, b2, sc2), run_oracle_bwa(b2, sc2), "209..256 columns")
+
+
 def test_width_limit_and_invalid_pairs(ctx):
     import paper_2301_09310_gb300 as xt
     rng = np.random.default_rng(3)

@@ -172,6 +172,33 @@ def test_host_variant(ctx):
     assert_same((out, cells), run_oracle(b, wl.scoring), "host variant")
 
 
+def test_host_variant_in_chunks(ctx):
+    # 2.2M pairs: the host call runs in chunks whose sequence bytes are copied
+    # while earlier chunks extend.  Its results must equal the device call's
+    # (itself pinned to the oracle), for pairs in buffer order and for pairs
+    # whose offsets jump around the buffers (every chunk then reads far ahead)
+    import torch
+    wl = synth.WORKLOADS["c3_mixed"]
+    b = synth.generate(wl, n=2_200_000, first=999)
+    sample = np.random.default_rng(1).choice(b.n, 4000, replace=False)
+    want_dev = run_gpu(ctx, b, wl.scoring)
+    sub = b.take(np.sort(sample))
+    assert_same((want_dev[0][np.sort(sample)], want_dev[1][np.sort(sample)]),
+                run_oracle(sub, wl.scoring), "device sample")
+
+    def pinned(a):
+        t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
+        t.numpy()[...] = a
+        return t.numpy()
+
+    perm = np.random.default_rng(2).permutation(b.n)
+    for order in (np.arange(b.n), perm):
+        h = [pinned(a) for a in (b.q_seq, b.q_off[order], b.q_len[order], b.t_seq,
+                                 b.t_off[order], b.t_len[order], b.h0[order])]
+        out, cells = ctx.extend_host(*h, wl.scoring)
+        assert_same((out, cells), (want_dev[0][order], want_dev[1][order]), "chunked host call")
+
+
 def test_repeat_calls_reuse_workspace(ctx):
     wl = synth.WORKLOADS["c2_short"]
     b1 = synth.generate(wl, n=2000, first=0)
