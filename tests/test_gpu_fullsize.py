@@ -57,3 +57,30 @@ def test_full_batch_sampled_against_oracle(ctx, name, sample):
     # the plain kernel agrees with the batched one on every pair
     pout, pcells = run_gpu(ctx, b, wl.scoring, plain=True)
     assert np.array_equal(pout, out) and np.array_equal(pcells, cells)
+
+
+def test_bwa_full_batch_sampled_against_oracle(ctx):
+    # the BWA-MEM-compatible call on the whole c3 batch, as bench.py times it
+    import torch
+    from paper_2301_09310_gb300.synth import BwaScoringParams
+
+    import oracle
+    from tests.gpu_util import to_dev
+    wl = synth.WORKLOADS["c3_mixed"]
+    b = synth.generate(wl)
+    sc = BwaScoringParams.from_scoring(wl.scoring)
+    o, c = ctx.extend_bwa(*to_dev(b, torch.device("cuda", ctx.device)), sc)
+    torch.cuda.synchronize()
+    out, cells = o.cpu().numpy(), c.cpu().numpy()
+    score, qle, tle, gscore, gtle, max_off, status = out.T
+    assert np.all(status == 0) and np.all(score >= b.h0) and np.all(cells >= 0)
+    assert np.all((qle <= b.q_len) & (tle <= b.t_len) & (gscore <= score) & (gscore >= -1))
+    rng = np.random.default_rng(2302)
+    idx = np.sort(rng.choice(b.n, size=6000, replace=False))
+    sub = b.take(idx)
+    want_out, want_cells = oracle.extend_batch_bwa(sub.q_seq, sub.q_off, sub.q_len, sub.t_seq,
+                                                   sub.t_off, sub.t_len, sub.h0,
+                                                   oracle.BwaScoring(*sc.as_tuple()))
+    bad = np.nonzero(np.any(out[idx] != want_out, axis=1) | (cells[idx] != want_cells))[0]
+    assert bad.size == 0, (f"{bad.size} of 6000 sampled pairs differ; first pair #{idx[bad[0]]}: "
+                           f"gpu {out[idx][bad[0]].tolist()} oracle {want_out[bad[0]].tolist()}")
