@@ -950,6 +950,7 @@ xt_status xt_extend_seeds(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_bytes, co
   if (s != XT_OK) return s;
   if (n_pairs > 0 && (!q_beg || !t_beg || !seed_len || !right))
     return fail(ctx, XT_EINVAL, "null array");
+  if (ctx->pending.active) return fail(ctx, XT_EBUSY, "a begun call has not been finished");
   if (n_pairs == 0) return XT_OK;
   cudaStream_t st = (cudaStream_t)stream;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, XT_ECUDA, "cudaSetDevice");
@@ -1018,6 +1019,7 @@ xt_status xt_extend_batch_host(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_byte
   xt_status s = check_args(ctx, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off, t_len, h0,
                            n_pairs, sc, out);
   if (s != XT_OK) return s;
+  if (ctx->pending.active) return fail(ctx, XT_EBUSY, "a begun call has not been finished");
   if (n_pairs == 0) return XT_OK;
   cudaStream_t st = (cudaStream_t)stream;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, XT_ECUDA, "cudaSetDevice");

@@ -624,6 +624,7 @@ extern "C" xt_status xt_extend_batch_bwa(xt_ctx* ctx, const uint8_t* q_seq, int6
     return ctx_fail(ctx, XT_EINVAL, "null array");
   if ((q_bytes > 0 && !q_seq) || (t_bytes > 0 && !t_seq))
     return ctx_fail(ctx, XT_EINVAL, "null sequence buffer");
+  if (ctx->pending.active) return ctx_fail(ctx, XT_EBUSY, "a begun call has not been finished");
   if (n_pairs == 0) return XT_OK;
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaSetDevice(ctx->device);

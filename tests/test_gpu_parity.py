@@ -274,6 +274,14 @@ def test_two_step_call(ctx):
             xt._scoring(wl.scoring), out.data_ptr(), cells.data_ptr(), st.cuda_stream)
     assert xt.xt_extend_batch_begin(ctx.handle, *args) == xt.XT_OK
     assert xt.xt_extend_batch(ctx.handle, *args) == xt.XT_EBUSY
+    # every other call of the context waits its turn too (they share the
+    # context's count read-back)
+    assert xt.xt_extend_batch_bwa(ctx.handle, *args[:10], (1, -4, -1, 6, 1, 6, 1, 100, 100, 5),
+                                  *args[11:]) == xt.XT_EBUSY
+    z = torch.zeros(b.n, dtype=torch.int32, device="cuda")
+    assert xt.xt_extend_seeds(ctx.handle, *args[:8], z.data_ptr(), z.data_ptr(), z.data_ptr(),
+                              d[6].data_ptr(), b.n, wl.scoring, out.data_ptr(), out.data_ptr(),
+                              0, 0, st.cuda_stream) == xt.XT_EBUSY
     for _ in range(20000):
         s, ready = xt.xt_extend_batch_ready(ctx.handle)
         assert s == xt.XT_OK
