@@ -230,7 +230,8 @@ xt_status xt_ctx_set_timing(xt_ctx* ctx, int enable);
  * CUDA graphs (on by default).  The second call with the same scoring,
  * schedule, capacity class (n rounded up to a power of two, at least 1024)
  * and workspace is captured as one graph; later such calls replay it, so a
- * call costs one small descriptor copy and one graph launch on the host.
+ * call costs the classify pass, one descriptor-store kernel and one graph
+ * launch on the host.
  * Calls with timing enabled launch directly.  enable = 0 turns capture off.
  * A context's calls must be ordered on the GPU (one stream, or synchronised):
  * they share its workspace.
