@@ -821,7 +821,7 @@ xt_status xt_ctx_create(xt_ctx** out, int device, size_t mem_budget_bytes) {
   c->smem_optin = max_smem_per_block_optin(device);
   bool ok = true;
   ok = ok && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
-  ok = ok && cudaHostAlloc((void**)&c->seg_host, 4096, cudaHostAllocDefault) == cudaSuccess;
+  ok = ok && cudaHostAlloc((void**)&c->seg_host, 4 * kSegHostWords, cudaHostAllocDefault) == cudaSuccess;
   ok = ok && cudaEventCreateWithFlags(&c->seg_ev, cudaEventDisableTiming) == cudaSuccess;
   ok = ok && cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) == cudaSuccess;
   for (int b = 0; ok && b < kMaxBranches; ++b) {
@@ -985,7 +985,7 @@ xt_status xt_extend_seeds(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_bytes, co
   // lengths and the prefix sums up to their totals, which size the copies
   cudaError_t e = launch_seed_front(n_pairs, q_len, t_len, q_off, t_off, q_bytes, t_bytes, q_beg,
                                     t_beg, seed_len, sw, st);
-  int64_t* tot_host = reinterpret_cast<int64_t*>(ctx->seg_host + 512);
+  int64_t* tot_host = reinterpret_cast<int64_t*>(ctx->seg_host + kSegHostSeedTotals);
   if (e == cudaSuccess) e = cudaMemcpyAsync(tot_host, sw.totals, 16, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaEventRecord(ctx->seg_ev, st);
   if (e == cudaSuccess) e = cudaEventSynchronize(ctx->seg_ev);
@@ -1091,7 +1091,7 @@ xt_status xt_extend_batch_host(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_byte
   if (e == cudaSuccess) e = cudaMemsetAsync(dends, 0, 16 * kMaxChunks, st);
   if (e == cudaSuccess)
     e = launch_chunk_ends(dqo, dql, dto, dtl, n_pairs, cp, q_bytes, t_bytes, dends, st);
-  unsigned long long* ends = reinterpret_cast<unsigned long long*>(ctx->seg_host + 768);
+  unsigned long long* ends = reinterpret_cast<unsigned long long*>(ctx->seg_host + kSegHostChunkEnds);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(ends, dends, 16 * kMaxChunks, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaEventRecord(ctx->seg_ev, st);

@@ -664,7 +664,7 @@ extern "C" xt_status xt_extend_batch_bwa(xt_ctx* ctx, const uint8_t* q_seq, int6
     e = cudaGetLastError();
   }
   // the class sizes come back to size the launches
-  int32_t* cnt_host = ctx->seg_host + 640;
+  int32_t* cnt_host = ctx->seg_host + kSegHostBwaCounts;
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(cnt_host, a.counts, 4 * kBwaClasses, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaEventRecord(ctx->seg_ev, st);

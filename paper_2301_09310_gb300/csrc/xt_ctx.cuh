@@ -50,6 +50,12 @@ struct TuneEntry {
 // Whether (P, R) is an instantiated schedule whose ring fits for bucket j
 // under band w on this context's device.
 bool bucket_sched_ok(const struct ::xt_ctx* ctx, int w, int j, int P, int R);
+// The context's pinned read-back area (int32 words): the bucket counts of a
+// batched call first, then the small values other calls bring back.
+constexpr int kSegHostWords = 1024;
+constexpr int kSegHostSeedTotals = 512;  // xt_extend_seeds: 2 x int64
+constexpr int kSegHostBwaCounts = 640;   // xt_extend_batch_bwa: class sizes
+constexpr int kSegHostChunkEnds = 768;   // xt_extend_batch_host: 2 x kMaxChunks x uint64
 // Drop every captured graph of the context.
 void drop_graphs(struct ::xt_ctx* ctx);
 // Record an error message on the context and return s (or XT_ECUDA for e).
@@ -65,6 +71,11 @@ xt_status ctx_codes(struct ::xt_ctx* ctx, const uint8_t** q_seq, int64_t q_bytes
 // Host-buffer calls of many pairs run in chunks of pairs whose sequence
 // bytes are copied while earlier chunks extend (xt_extend_batch_host).
 constexpr int kMaxChunks = 8;
+// the read-back regions do not overlap (bucket counts: two aligned tables)
+static_assert(2 * (4 * kNumClasses * kNumJ + 255) / 4 <= kSegHostSeedTotals, "bucket counts");
+static_assert(kSegHostSeedTotals + 4 <= kSegHostBwaCounts, "seed totals");
+static_assert(kSegHostBwaCounts + 16 <= kSegHostChunkEnds, "BWA class sizes");
+static_assert(kSegHostChunkEnds + 4 * kMaxChunks <= kSegHostWords, "chunk ends");
 constexpr int32_t kChunkPairs = 1 << 20;   // pairs per chunk at least (a chunk fills the GPU)
 // ends[2k], ends[2k+1]: how far chunk k's pairs read into the query and the
 // target buffer (see xt_stage.cu); ends must be zeroed first.
