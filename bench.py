@@ -84,7 +84,7 @@ def parse_args():
     ap.add_argument("--streams", type=int, default=0,
                     help="streams the extension kernels of a call fork onto (0: library default)")
     ap.add_argument("--serve-slots", type=int, default=3)
-    ap.add_argument("--serve-batch-mib", type=int, default=128,
+    ap.add_argument("--serve-batch-mib", type=int, default=256,
                     help="staged bytes per batch (the slot capacity), MiB")
     ap.add_argument("--serve-budget-gb", type=float, default=40.0,
                     help="device memory budget of the whole server, GB")

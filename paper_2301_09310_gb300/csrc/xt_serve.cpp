@@ -428,7 +428,7 @@ xt_status xt_serve_create(xt_server** out, int device, const xt_serve_config* cf
   if (cfg_in) cfg = *cfg_in;
   if (cfg.slots == 0) cfg.slots = 3;
   if (cfg.max_batch_pairs == 0) cfg.max_batch_pairs = 1 << 20;
-  if (cfg.max_batch_bytes == 0) cfg.max_batch_bytes = (int64_t)128 << 20;
+  if (cfg.max_batch_bytes == 0) cfg.max_batch_bytes = (int64_t)256 << 20;
   if (cfg.max_queued_bytes == 0) cfg.max_queued_bytes = (int64_t)1 << 30;
   if (cfg.gather_threads == 0) {
     const int hw = (int)std::thread::hardware_concurrency();
