@@ -412,7 +412,10 @@ def run_xt(args):
     res = {
         "metric": METRIC, "value": round(value, 3), "unit": "GCUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        # packed 16-bit lanes where the score bound allows, 32-bit otherwise
+        "dtype": ("int16x2" if packed_frac >= 1.0 else
+                  "int32" if packed_frac <= 0.0 else "int16x2+int32"),
         "data": "synthetic",
         "config": {"workload": f"{wl.name}: {WORKLOAD_TEXT.get(wl.name, '')}",
                    "pairs_per_gpu": n, "scoring": wl.scoring.as_tuple(),
