@@ -311,3 +311,34 @@ def test_trimming_and_move_rules_only_remove_paths():
                                    trace=True) if w == sc.w else full
         m = min(len(nb.row_m), len(d.row_m))
         assert np.all(nb.H[1:m + 1, 1:] <= d.H[1:m + 1, 1:])
+
+
+def test_batch_runner_width_limit_and_checks():
+    # the batch runner rejects pairs whose rows would exceed 8,192 columns
+    # (min(qlen, 2w'+1)), invalid offsets and h0 < 1, and agrees with the
+    # single-pair call on the rest
+    rng = np.random.default_rng(11)
+    qs = [rng.integers(0, 4, 9000), rng.integers(0, 4, 8192), rng.integers(0, 4, 40),
+          rng.integers(0, 4, 30)]
+    ts = [rng.integers(0, 4, 40), rng.integers(0, 4, 30), rng.integers(0, 4, 60),
+          rng.integers(0, 4, 30)]
+    h0 = np.array([20, 20, 20, 0], np.int32)
+    ql = np.array([q.size for q in qs], np.int32)
+    tl = np.array([t.size for t in ts], np.int32)
+    qo = np.concatenate([[0], np.cumsum(ql[:-1])]).astype(np.int64)
+    to = np.concatenate([[0], np.cumsum(tl[:-1])]).astype(np.int64)
+    q_seq = np.concatenate(qs).astype(np.uint8)
+    t_seq = np.concatenate(ts).astype(np.uint8)
+    sc = BwaScoring(w=5000, zdrop=0)
+    out, cells = oracle.extend_batch_bwa(q_seq, qo, ql, t_seq, to, tl, h0, sc, nthreads=2)
+    assert out[0, 6] == 1 and cells[0] == 0          # 9,000 columns
+    assert out[3, 6] == 1                             # h0 = 0
+    for k in (1, 2):                                  # 8,192 columns is still accepted
+        assert out[k, 6] == 0
+        res, c = oracle.extend_one_bwa(qs[k], ts[k], 20, sc)
+        assert tuple(out[k]) == res and cells[k] == c
+    # with a narrow band the long query fits
+    out2, _ = oracle.extend_batch_bwa(q_seq, qo, ql, t_seq, to, tl, h0, BwaScoring(w=100))
+    assert out2[0, 6] == 0
+    with pytest.raises(ValueError):
+        oracle.extend_batch_bwa(q_seq, qo, ql, t_seq, to, tl, h0, BwaScoring(e_ins=0))
