@@ -173,6 +173,7 @@ def test_host_variant(ctx):
 
 
 def test_host_variant_in_chunks(ctx):
+    import paper_2301_09310_gb300 as xt
     # 2.2M pairs: the host call runs in chunks whose sequence bytes are copied
     # while earlier chunks extend.  Its results must equal the device call's
     # (itself pinned to the oracle), for pairs in buffer order and for pairs
@@ -197,6 +198,18 @@ def test_host_variant_in_chunks(ctx):
                                  b.t_off[order], b.t_len[order], b.h0[order])]
         out, cells = ctx.extend_host(*h, wl.scoring)
         assert_same((out, cells), (want_dev[0][order], want_dev[1][order]), "chunked host call")
+    # pairs outside their buffers (in the first and the last chunk) are
+    # rejected, the rest unchanged
+    qo, to = b.q_off.copy(), b.t_off.copy()
+    qo[5] = b.q_seq.size + 100
+    to[b.n - 3] = -7
+    h = [pinned(a) for a in (b.q_seq, qo, b.q_len, b.t_seq, to, b.t_len, b.h0)]
+    out, cells = ctx.extend_host(*h, wl.scoring)
+    assert out[5, 6] == xt.XT_EINVAL and out[b.n - 3, 6] == xt.XT_EINVAL
+    keep = np.ones(b.n, bool)
+    keep[[5, b.n - 3]] = False
+    assert np.array_equal(out[keep], want_dev[0][keep]) and np.array_equal(cells[keep],
+                                                                           want_dev[1][keep])
 
 
 def test_repeat_calls_reuse_workspace(ctx):
