@@ -173,12 +173,12 @@ def test_host_variant(ctx):
 
 
 def test_host_variant_in_chunks(ctx):
-    import paper_2301_09310_gb300 as xt
     # 2.2M pairs: the host call runs in chunks whose sequence bytes are copied
     # while earlier chunks extend.  Its results must equal the device call's
     # (itself pinned to the oracle), for pairs in buffer order and for pairs
     # whose offsets jump around the buffers (every chunk then reads far ahead)
     import torch
+    import paper_2301_09310_gb300 as xt
     wl = synth.WORKLOADS["c3_mixed"]
     b = synth.generate(wl, n=2_200_000, first=999)
     sample = np.random.default_rng(1).choice(b.n, 4000, replace=False)
