@@ -513,9 +513,11 @@ __device__ __forceinline__ void bwa_pair(const BwaArgs& a, const Group<G>& g, in
   if (lane == 0) put_result(a, k, best, bj + 1, bi + 1, gscore, gtle, max_off, XT_OK, cells);
 }
 
+// Four CTAs per SM (128 registers, no spills) rather than three: the kernel
+// is bound by the integer pipe and waits on short dependency chains.
 template <int G>
-__global__ void __launch_bounds__(kBwaWarpThreads) k_bwa_seg(BwaArgs a, int cls, int32_t off,
-                                                             int32_t count) {
+__global__ void __launch_bounds__(kBwaWarpThreads, 4) k_bwa_seg(BwaArgs a, int cls, int32_t off,
+                                                                int32_t count) {
   Group<G> g;
   g.init();
   for (;;) {
@@ -529,8 +531,10 @@ __global__ void __launch_bounds__(kBwaWarpThreads) k_bwa_seg(BwaArgs a, int cls,
   }
 }
 
+// 512 threads per SM at least (16 warps, 128 registers each).
 template <int G>
-__global__ void __launch_bounds__(G) k_bwa_cta(BwaArgs a, int cls, int32_t off, int32_t count) {
+__global__ void __launch_bounds__(G, 512 / G) k_bwa_cta(BwaArgs a, int cls, int32_t off,
+                                                        int32_t count) {
   __shared__ typename Group<G, false>::Shared s;
   Group<G> g;
   g.init(&s);
