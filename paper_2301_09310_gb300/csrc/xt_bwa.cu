@@ -14,18 +14,17 @@
 //    apply.
 //
 // So one pair is extended by a group of G lanes that computes a whole row at
-// a time: lane l holds K consecutive columns of the row in registers (slot s =
-// l*K + k is column A_i + s, with the anchor A_i = max(0, i - w') the first
-// in-band column of row i).  Going from row i-1 to row i the anchor moves by
-// 0 or 1 column, so the row above sits at the same slot (diagonal neighbour)
-// or one slot further (vertical neighbour): one shuffle across each lane
-// boundary.  Per row the group runs an exclusive max-scan for the insertion
+// a time, and only the row's own columns [beg, end): trimming keeps a row far
+// narrower than its band (about a quarter of 2w'+1 on short reads), so the
+// lanes split the row's width, k = ceil((end - beg) / G) <= K consecutive
+// columns each, and the row above lives in shared memory rather than in fixed
+// registers.  Per row the group runs an exclusive max-scan for the insertion
 // chain, a max-reduction for the row maximum and its column, and a min/max
-// reduction for the live run.  G is the smallest power of two with G*K >=
-// min(qlen, 2w'+1), from 4 lanes (64 columns) to 512 lanes (8192 columns); up
-// to 32 lanes a group is a warp segment (shuffles), above that a whole CTA
-// (shuffles plus shared memory).  Pairs are classified by G, and each class
-// runs a persistent kernel whose groups take pairs from a counter.
+// reduction for the live run.  G*K is the smallest power of two >= min(qlen,
+// 2w'+1), from 64 to 8192 columns; up to 32 lanes a group is a warp segment
+// (shuffles), above that a whole CTA (shuffles plus shared memory).  Pairs are
+// classified by G*K, and each class runs a persistent kernel whose groups take
+// pairs from a counter.
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -38,8 +37,15 @@
 namespace xt {
 namespace {
 
-constexpr int kBwaK = 16;                    // columns per lane
-constexpr int kBwaClasses = 8;               // G = 4 << class, 64 << class columns
+// Most columns a lane computes in a row (16 or 32): more columns per lane
+// means fewer lanes per pair and cheaper per-row collectives, at two
+// registers per column.
+#ifndef XT_BWA_LANE_COLUMNS
+#define XT_BWA_LANE_COLUMNS 32
+#endif
+constexpr int kBwaK = XT_BWA_LANE_COLUMNS;
+static_assert(kBwaK == 16 || kBwaK == 32, "columns per lane: 16 or 32");
+constexpr int kBwaClasses = 8;               // G*K = 64 << class columns
 constexpr int kBwaWarpThreads = 128;         // CTA size of the warp-segment classes
 constexpr int32_t kBwaNeg = -(1 << 29);      // below any reachable value
 constexpr uint8_t kBwaDone = 0xff;           // pair finished in classify
@@ -175,16 +181,8 @@ struct Group<G, true> {
     mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (wl & ~(G - 1)));
   }
   __device__ __forceinline__ int index() const { return lane; }
-  // value of lane l+1 (0 past the last lane)
-  __device__ __forceinline__ int32_t from_next(int32_t v) const {
-    const int32_t r = __shfl_down_sync(mask, v, 1, G);
-    return lane == G - 1 ? 0 : r;
-  }
-  // value of lane l-1 (fill for lane 0)
-  __device__ __forceinline__ int32_t from_prev(int32_t v, int32_t fill) const {
-    const int32_t r = __shfl_up_sync(mask, v, 1, G);
-    return lane == 0 ? fill : r;
-  }
+  // orders the group's shared-memory accesses before and after it
+  __device__ __forceinline__ void sync() const { __syncwarp(mask); }
   // max over the lanes before this one (kBwaNeg for lane 0)
   __device__ __forceinline__ int32_t excl_max(int32_t v) const {
 #pragma unroll
@@ -211,9 +209,6 @@ struct Group<G, true> {
       *b = min(*b, __shfl_xor_sync(mask, *b, o, G));
     }
   }
-  __device__ __forceinline__ int32_t bcast(int32_t v, int src) const {
-    return __shfl_sync(mask, v, src, G);
-  }
   // one lane takes the next pair of the class for the whole group
   __device__ __forceinline__ int32_t claim(int32_t* head) const {
     int32_t p = 0;
@@ -222,7 +217,7 @@ struct Group<G, true> {
   }
 };
 
-// A whole CTA of G lanes (G = 64 .. 512): shuffles inside warps, shared memory
+// A whole CTA of G lanes (G >= 64): shuffles inside warps, shared memory
 // across them.  Each collective writes its own shared array once per row and
 // ends with one barrier; at least one other barrier separates two uses of the
 // same array, so a lane can never overwrite a value another lane still reads.
@@ -230,12 +225,9 @@ template <int G>
 struct Group<G, false> {
   static constexpr int kW = G / 32;
   struct Shared {
-    int32_t nxt[3][kW];
-    int32_t prv[kW];
     int32_t scan[kW];
     int64_t key[kW];
     int32_t amax[kW], amin[kW];
-    int32_t b;
     int32_t claim;
   };
   Shared* sh;
@@ -247,33 +239,7 @@ struct Group<G, false> {
     wid = lane >> 5;
   }
   __device__ __forceinline__ int index() const { return lane; }
-  // values of lane l+1 for three registers at once (0 past the last lane)
-  __device__ __forceinline__ void from_next3(int32_t* a, int32_t* b, int32_t* c) const {
-    if (wl == 0) {
-      sh->nxt[0][wid] = *a;
-      sh->nxt[1][wid] = *b;
-      sh->nxt[2][wid] = *c;
-    }
-    const int32_t ra = __shfl_down_sync(0xffffffffu, *a, 1);
-    const int32_t rb = __shfl_down_sync(0xffffffffu, *b, 1);
-    const int32_t rc = __shfl_down_sync(0xffffffffu, *c, 1);
-    __syncthreads();
-    if (wl == 31) {
-      const bool last = wid == kW - 1;
-      *a = last ? 0 : sh->nxt[0][wid + 1];
-      *b = last ? 0 : sh->nxt[1][wid + 1];
-      *c = last ? 0 : sh->nxt[2][wid + 1];
-    } else {
-      *a = ra; *b = rb; *c = rc;
-    }
-  }
-  __device__ __forceinline__ int32_t from_prev(int32_t v, int32_t fill) const {
-    if (wl == 31) sh->prv[wid] = v;
-    const int32_t r = __shfl_up_sync(0xffffffffu, v, 1);
-    __syncthreads();
-    if (wl == 0) return wid == 0 ? fill : sh->prv[wid - 1];
-    return r;
-  }
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
   __device__ __forceinline__ int32_t excl_max(int32_t v) const {
     int32_t inc = v;
 #pragma unroll
@@ -319,11 +285,6 @@ struct Group<G, false> {
     *a = x;
     *b = y;
   }
-  __device__ __forceinline__ int32_t bcast(int32_t v, int src) const {
-    if (lane == src) sh->b = v;
-    __syncthreads();
-    return sh->b;
-  }
   __device__ __forceinline__ int32_t claim(int32_t* head) const {
     __syncthreads();  // the previous pair's readers of sh->claim are done
     if (lane == 0) sh->claim = atomicAdd(head, 1);
@@ -332,57 +293,34 @@ struct Group<G, false> {
   }
 };
 
-template <int G>
-__device__ __forceinline__ void shift_in(const Group<G, true>& g, int32_t* a, int32_t* b,
-                                         int32_t* c) {
-  *a = g.from_next(*a);
-  *b = g.from_next(*b);
-  *c = g.from_next(*c);
-}
-template <int G>
-__device__ __forceinline__ void shift_in(const Group<G, false>& g, int32_t* a, int32_t* b,
-                                         int32_t* c) {
-  g.from_next3(a, b, c);
-}
-
-// Score row for target code ti (0..4): byte c = S(ti, query code c), c = 0..4.
-__device__ __forceinline__ void score_row(const BwaScore& s, uint32_t ti, uint32_t* lo,
-                                          uint32_t* hi) {
-  const uint32_t nb = (uint8_t)(int8_t)s.nsc;
+// Score row for target code ti (0..4) as biased bytes: byte c of {hi:lo} is
+// S(ti, query code c) + 128, c = 0..4; bytes 5..7 are 0.
+__device__ __forceinline__ void score_row(uint32_t ti, uint32_t mism4, uint32_t nb, uint32_t mb,
+                                          uint32_t* lo, uint32_t* hi) {
   if (ti >= 4u) {
     *lo = nb * 0x01010101u;
   } else {
-    const uint32_t xb = (uint8_t)(int8_t)s.mismatch, mb = (uint8_t)(int8_t)s.match;
     const uint32_t sh = 8u * ti;
-    *lo = ((xb * 0x01010101u) & ~(0xffu << sh)) | (mb << sh);
+    *lo = (mism4 & ~(0xffu << sh)) | (mb << sh);
   }
   *hi = nb;
 }
 
-// M and F of slot s from its diagonal (D) and vertical (um, uf) neighbours in
-// the row above, 0 outside the row's columns [lo, hi); Y carries the lane's
-// insertion chain (started from 0 at its first slot) past the slot.
-__device__ __forceinline__ void cell_mf(const BwaScore& sc, int32_t s, int32_t lo, int32_t hi,
-                                        uint32_t rp_lo, uint32_t rp_hi, uint32_t sel, int32_t D,
-                                        int32_t um, int32_t uf, int32_t oe_del, int32_t e_del,
-                                        int32_t oe_ins, int32_t e_ins, int32_t* M_out,
-                                        int32_t* F_out, int32_t* Y) {
-  const bool in = (uint32_t)(s - lo) < (uint32_t)(hi - lo);
-  const int32_t S = prmt_s8(rp_lo, rp_hi, sel);
-  const int32_t M = (in && D > 0) ? D + S : 0;
-  *F_out = in ? __viaddmax_s32_relu(um, -oe_del, uf - e_del) : 0;
-  *M_out = M;
-  *Y = __viaddmax_s32_relu(M, -oe_ins, *Y - e_ins);
-}
-
 // --------------------------------------------------------------- the kernel
-// One pair per group of G lanes; slot s = lane*K + k of row i is column
-// A_i + s.  Registers per slot: H, M, F of the row above (under its anchor)
-// and the query base's score selector (under the current anchor).
-template <int G>
-__device__ __forceinline__ void bwa_pair(const BwaArgs& a, const Group<G>& g, int32_t k) {
-  constexpr int K = kBwaK;
-  constexpr int C = G * K;
+// One pair per group of G lanes.  Row i computes only its columns [beg, end):
+// lane l takes the k = ceil((end - beg) / G) consecutive columns from
+// beg + l*k (fewer in the last lanes).  The row above lives in the group's
+// buffer of G*K + 2 elements, one per column j of [beg - 1, end]: x = H(i-1, j)
+// and y = F(i, j) << 4 | query code of column j, at index j - o(i-1) with the
+// origin o(r) = max(-1, r - w' - 1).  The origin moves by 0 or 1 column a
+// row, so a row's reads (x of column j-1, y of column j) and its writes (column
+// j at index j - o(i)) touch the same window; a barrier of the group separates
+// the row's reads from its writes.  Two extra elements per row hold the
+// boundary: column beg-1 (x = H of column -1 for the next row: the deletion
+// run from the seed, else 0) and column end (y = 0 | its query code).
+template <int G, int K>
+__device__ __forceinline__ void bwa_pair(const BwaArgs& a, const Group<G>& g, int2* buf,
+                                         int32_t k) {
   const BwaScore& sc = a.sc;
   const int32_t qlen = a.q_len[k], tlen = a.t_len[k], h0 = a.h0[k];
   const uint8_t* q = a.q_seq + a.q_off[k];
@@ -390,91 +328,97 @@ __device__ __forceinline__ void bwa_pair(const BwaArgs& a, const Group<G>& g, in
   const int32_t w = bwa_band(sc, qlen);
   const int32_t oe_ins = sc.o_ins + sc.e_ins, oe_del = sc.o_del + sc.e_del;
   const int32_t e_ins = sc.e_ins, e_del = sc.e_del;
+  const uint32_t mb = (uint32_t)(sc.match + 128), nb = (uint32_t)(sc.nsc + 128);
+  const uint32_t mism4 = (uint32_t)(sc.mismatch + 128) * 0x01010101u;
   const int lane = g.index();
-  const int32_t sb = lane * K;  // this lane's first slot
 
-  int32_t Hd[K], Mv[K], Fv[K];
-  uint32_t qs[K];
-  // row -1 under anchor 0: the insertion run from the seed, inside the band
-#pragma unroll
-  for (int kk = 0; kk < K; ++kk) {
-    const int32_t s = sb + kk;
-    const int32_t v = h0 - oe_ins - e_ins * s;
-    Hd[kk] = (s < qlen && s + 1 <= w && v > 0) ? v : 0;
-    Mv[kk] = 0;
-    Fv[kk] = 0;
-    qs[kk] = score_selector(s < qlen ? clamp_code(q[s]) : 4u);
+  // row -1 (origin -1): the seed at column -1, the insertion run from it
+  // inside the band, no deletion state; each element carries its column's code
+  int32_t end = min(qlen, w + 1);
+  for (int32_t idx = lane; idx < end + 2; idx += G) {
+    const int32_t j = idx - 1;
+    int32_t x = h0;
+    if (j >= 0) {
+      const int32_t v = h0 - oe_ins - e_ins * j;
+      x = (j < qlen && j + 1 <= w && v > 0) ? v : 0;
+    }
+    const int32_t c = (j >= 0 && j < qlen) ? (int32_t)clamp_code(q[j]) : 4;
+    buf[idx] = make_int2(x, c);
   }
-  int32_t A_prev = 0;
-  int32_t hb_prev = h0;  // column -1 of the row above: the seed for row 0
-  int32_t beg = 0, end = min(qlen, w + 1);
+  g.sync();
+  int32_t beg = 0;
   int32_t best = h0, bi = -1, bj = -1, max_off = 0, gscore = -1, gtle = 0;
   int64_t cells = 0;
+  uint32_t t_next = tlen > 0 ? t[0] : 4u;
 
   for (int32_t i = 0; i < tlen; ++i) {
     if (beg >= end) break;  // nothing to compute: the row maximum is 0
-    const int32_t A = max(0, i - w);
-    const int32_t lo = beg - A, hi = end - A;
+    const int32_t o_up = max(-1, i - w - 2), o_row = max(-1, i - w - 1);
     uint32_t rp_lo, rp_hi;
-    score_row(sc, clamp_code(t[i]), &rp_lo, &rp_hi);
-    // pass 1: M and F per slot from the row above (diagonal and vertical
-    // neighbours), and the lane's insertion carry from 0
+    score_row(clamp_code(t_next), mism4, nb, mb, &rp_lo, &rp_hi);
+    if (i + 1 < tlen) t_next = t[i + 1];
+    // the query code of column end enters with the row's boundary element
+    const int32_t q_end = (lane == G - 1 && end < qlen) ? (int32_t)clamp_code(q[end]) : 4;
+    const int32_t kq = (end - beg + G - 1) / G;  // <= K: end - beg <= min(qlen, 2w'+1)
+    const int32_t first = beg + lane * kq;
+    const int32_t cnt = max(0, min(kq, end - first));
+
+    // pass 1: M, F and H without the insertion carry from earlier lanes;
+    // Y is the lane's insertion chain, started from 0
+    int32_t Hp[K], Yn[K];
     int32_t Y = 0;
-    if (A == A_prev) {
-      const int32_t in = g.from_prev(Hd[K - 1], hb_prev);
+    if (cnt > 0) {
+      const int2* rd = buf + (first - 1 - o_up);
+      int32_t Dn = rd[0].x;
 #pragma unroll
       for (int kk = 0; kk < K; ++kk) {
-        const int32_t D = kk > 0 ? Hd[kk - 1] : in;
-        cell_mf(sc, sb + kk, lo, hi, rp_lo, rp_hi, qs[kk], D, Mv[kk], Fv[kk], oe_del, e_del,
-                oe_ins, e_ins, &Mv[kk], &Fv[kk], &Y);
-      }
-    } else {
-      // the anchor moved one column right: the row above is one slot further
-      int32_t m0 = Mv[0], f0 = Fv[0], q0 = (int32_t)qs[0];
-      shift_in(g, &m0, &f0, &q0);
-#pragma unroll
-      for (int kk = 0; kk < K; ++kk) qs[kk] = kk + 1 < K ? qs[kk + 1] : (uint32_t)q0;
-      if (lane == G - 1) {
-        const int32_t c = A + C - 1;
-        qs[K - 1] = score_selector(c < qlen ? clamp_code(q[c]) : 4u);
-      }
-#pragma unroll
-      for (int kk = 0; kk < K; ++kk) {
-        const int32_t um = kk + 1 < K ? Mv[kk + 1] : m0;
-        const int32_t uf = kk + 1 < K ? Fv[kk + 1] : f0;
-        cell_mf(sc, sb + kk, lo, hi, rp_lo, rp_hi, qs[kk], Hd[kk], um, uf, oe_del, e_del, oe_ins,
-                e_ins, &Mv[kk], &Fv[kk], &Y);
+        if (kk >= cnt) break;
+        const int2 e = rd[kk + 1];
+        const int32_t D = Dn;
+        Dn = e.x;
+        const uint32_t code = (uint32_t)e.y & 15u;
+        const int32_t Sb = prmt_s8(rp_lo, rp_hi, code | 0x5550u);
+        const int32_t M = D > 0 ? D + Sb - 128 : 0;
+        const int32_t F = e.y >> 4;
+        const int32_t Fn = __viaddmax_s32_relu(M, -oe_del, F - e_del);
+        Yn[kk] = (int32_t)(((uint32_t)Fn << 4) | code);
+        Hp[kk] = __vimax3_s32(M, Y, F);
+        Y = __viaddmax_s32_relu(M, -oe_ins, Y - e_ins);
       }
     }
     // insertion carry into this lane: max over earlier lanes l' of their
-    // carry Y_l' decayed over the (l - 1 - l') * K columns in between
-    const int32_t decay = e_ins * K;
+    // carry Y_l' decayed over the (l - 1 - l') * k columns in between
+    const int32_t decay = e_ins * kq;
     const int32_t ex = g.excl_max(Y + decay * lane);
     int32_t E = lane == 0 ? 0 : max(0, ex - decay * (lane - 1));
-    // pass 2: E, H, the row maximum (largest slot on ties) and the live mask
-    int32_t key = 0;
-    uint32_t live = 0;
+    g.sync();  // every read of the row above is done
+    // pass 2: H, the lane's maximum (largest column on ties), dead columns
+    int32_t Hl = -1, kl = 0;
+    uint32_t dead = 0;
+    if (cnt > 0) {
+      int2* wr = buf + (first - o_row);
 #pragma unroll
-    for (int kk = 0; kk < K; ++kk) {
-      const int32_t s = sb + kk;
-      const bool in = (uint32_t)(s - lo) < (uint32_t)(hi - lo);
-      const int32_t M = Mv[kk];
-      const int32_t H = in ? __vimax3_s32(M, E, Fv[kk]) : 0;
-      Hd[kk] = H;
-      key = max(key, H * K + kk);
-      live |= H > 0 ? 1u << kk : 0u;
-      E = __viaddmax_s32_relu(M, -oe_ins, E - e_ins);
+      for (int kk = 0; kk < K; ++kk) {
+        if (kk >= cnt) break;
+        const int32_t H = max(Hp[kk], E);
+        E -= e_ins;
+        const bool ge = H >= Hl;
+        Hl = ge ? H : Hl;
+        kl = ge ? kk : kl;
+        dead |= H == 0 ? 1u << kk : 0u;
+        wr[kk] = make_int2(H, Yn[kk]);
+      }
     }
-    const int64_t kk64 = g.all_max64(((int64_t)(key / K) << 32) | (uint32_t)(sb + key % K));
-    const int32_t m = (int32_t)(kk64 >> 32);
-    const int32_t mslot = (int32_t)(kk64 & 0xffffffff);
+    const int32_t hb = (beg == 0 && i + 1 <= w) ? max(0, h0 - oe_del - e_del * i) : 0;
+    if (lane == 0) buf[beg - 1 - o_row] = make_int2(hb, 4);
+    if (lane == G - 1) buf[end - o_row] = make_int2(0, q_end);
+    const int64_t key = g.all_max64(((int64_t)Hl << 32) | (uint32_t)(first + kl));
+    const int32_t m = (int32_t)(key >> 32);
+    const int32_t mj = (int32_t)(key & 0xffffffff);
+    g.sync();  // the row is stored
     // end-to-end score when the row reaches the last query column
     if (end == qlen) {
-      const int32_t ts = qlen - 1 - A;
-      int32_t gv = 0;
-#pragma unroll
-      for (int kk = 0; kk < K; ++kk) gv = (sb + kk == ts) ? Hd[kk] : gv;
-      gv = g.bcast(gv, ts / K);
+      const int32_t gv = buf[qlen - 1 - o_row].x;
       if (gv >= gscore) {
         gscore = gv;
         gtle = i + 1;
@@ -482,7 +426,6 @@ __device__ __forceinline__ void bwa_pair(const BwaArgs& a, const Group<G>& g, in
     }
     if (m == 0) break;
     cells += end - beg;
-    const int32_t mj = A + mslot;
     if (m > best) {
       best = m;
       bi = i;
@@ -494,97 +437,117 @@ __device__ __forceinline__ void bwa_pair(const BwaArgs& a, const Group<G>& g, in
                                    : (int64_t)best - m - (dj - di) * e_ins;
       if (drop > sc.zdrop) break;
     }
-    // the live run around the best slot: the last dead slot below it and the
-    // first dead slot above it (slots outside [lo, hi) hold 0)
-    const int32_t rel = mslot - sb;
-    const uint32_t dead = ~live & ((1u << K) - 1u);
-    const uint32_t below = rel <= 0 ? 0u : (rel >= K ? dead : dead & ((1u << rel) - 1u));
-    const uint32_t above = rel >= K - 1 ? 0u : (rel < 0 ? dead : dead & ~((2u << rel) - 1u));
-    int32_t zb = below ? sb + 31 - __clz(below) : -1;
-    int32_t za = above ? sb + __ffs(above) - 1 : C;
+    // the live run around the best column: the last dead column below it and
+    // the first dead column above it (columns outside [beg, end) are dead)
+    const int32_t rel = mj - first;
+    const uint32_t below = rel <= 0 ? 0u : (rel >= cnt ? dead : dead & ((1u << rel) - 1u));
+    const uint32_t above =
+        rel >= cnt - 1 ? 0u : (rel < 0 ? dead : dead & ~((2u << rel) - 1u));
+    int32_t zb = below ? first + 31 - __clz(below) : beg - 1;
+    int32_t za = above ? first + __ffs(above) - 1 : end;
     g.all_max_min(&zb, &za);
     // next row: the run's columns reachable in one step, within the band
-    const int32_t hb = (beg == 0 && i + 1 <= w) ? max(0, h0 - oe_del - e_del * i) : 0;
-    beg = max(A + zb + 1, i + 1 - w);
-    end = min(min(A + za + 1, i + w + 2), qlen);
-    hb_prev = hb;
-    A_prev = A;
+    beg = max(zb + 1, i + 1 - w);
+    end = min(min(za + 1, i + w + 2), qlen);
   }
   if (lane == 0) put_result(a, k, best, bj + 1, bi + 1, gscore, gtle, max_off, XT_OK, cells);
+  g.sync();  // the buffer is free for the group's next pair
 }
 
-// Four CTAs per SM (128 registers, no spills) rather than three: the kernel
-// is bound by the integer pipe and waits on short dependency chains.
-template <int G>
-__global__ void __launch_bounds__(kBwaWarpThreads, 4) k_bwa_seg(BwaArgs a, int cls, int32_t off,
+// Columns per lane K and lanes per pair G of a class (capacity 64 << class).
+template <int C>
+struct BwaClass {
+  static constexpr int K = kBwaK;
+  static constexpr int G = (64 << C) / K;
+  static constexpr bool kSeg = G <= 32;
+  static constexpr int kPairsPerBlock = kSeg ? kBwaWarpThreads / G : 1;
+  static constexpr int kBufElems = G * K + 2;  // per pair
+  static constexpr int kThreads = kSeg ? kBwaWarpThreads : G;
+  static constexpr size_t kSmem = (size_t)kPairsPerBlock * kBufElems * sizeof(int2);
+};
+
+// Four CTAs per SM (128 registers) for the warp-segment classes.
+template <int C>
+__global__ void __launch_bounds__(kBwaWarpThreads, 4) k_bwa_seg(BwaArgs a, int32_t off,
                                                                 int32_t count) {
+  using Cl = BwaClass<C>;
+  constexpr int G = Cl::G;
+  __shared__ int2 s_buf[Cl::kPairsPerBlock * Cl::kBufElems];
   Group<G> g;
   g.init();
+  int2* buf = s_buf + (threadIdx.x / G) * Cl::kBufElems;
   for (;;) {
-    const int32_t p = g.claim(&a.heads[cls]);
+    const int32_t p = g.claim(&a.heads[C]);
     if (p >= count) break;
     const int32_t idx = off + p;
     if (idx < 0 || idx >= a.n) break;  // defensive: order index out of range
     const int32_t k = a.order[idx];
     if (k < 0 || k >= a.n) continue;
-    bwa_pair<G>(a, g, k);
+    bwa_pair<G, Cl::K>(a, g, buf, k);
   }
 }
 
-// 512 threads per SM at least (16 warps, 128 registers each).
-template <int G>
-__global__ void __launch_bounds__(G, 512 / G) k_bwa_cta(BwaArgs a, int cls, int32_t off,
-                                                        int32_t count) {
+// One pair per CTA; the row buffer in dynamic shared memory.
+template <int C>
+__global__ void __launch_bounds__(BwaClass<C>::G, 512 / BwaClass<C>::G)
+    k_bwa_cta(BwaArgs a, int32_t off, int32_t count) {
+  using Cl = BwaClass<C>;
+  constexpr int G = Cl::G;
   __shared__ typename Group<G, false>::Shared s;
+  extern __shared__ int2 d_buf[];
   Group<G> g;
   g.init(&s);
   for (;;) {
-    const int32_t p = g.claim(&a.heads[cls]);
+    const int32_t p = g.claim(&a.heads[C]);
     if (p >= count) break;
     const int32_t idx = off + p;
     if (idx < 0 || idx >= a.n) break;
     const int32_t k = a.order[idx];
     if (k < 0 || k >= a.n) continue;
-    bwa_pair<G>(a, g, k);
+    bwa_pair<G, Cl::K>(a, g, d_buf, k);
   }
 }
 
-template <int G>
-cudaError_t launch_class(xt_ctx* ctx, const BwaArgs& a, int cls, int32_t off, int32_t count,
+template <int C>
+cudaError_t launch_class(xt_ctx* ctx, const BwaArgs& a, int32_t off, int32_t count,
                          cudaStream_t stream) {
-  constexpr bool kSeg = G <= 32;
-  const int threads = kSeg ? kBwaWarpThreads : G;
-  const int per_block = kSeg ? kBwaWarpThreads / G : 1;
-  int& resident = ctx->bwa_blocks[cls];
+  using Cl = BwaClass<C>;
+  int& resident = ctx->bwa_blocks[C];
+  const size_t dyn = Cl::kSeg ? 0 : Cl::kSmem;
   if (resident == 0) {
     cudaError_t e;
-    if constexpr (kSeg)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_bwa_seg<G>, threads, 0);
-    else
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_bwa_cta<G>, threads, 0);
+    if constexpr (Cl::kSeg) {
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_bwa_seg<C>, Cl::kThreads, 0);
+    } else {
+      e = cudaFuncSetAttribute(k_bwa_cta<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)dyn);
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_bwa_cta<C>, Cl::kThreads,
+                                                          dyn);
+    }
     if (e != cudaSuccess) return e;
     if (resident < 1) resident = 1;
   }
-  const int64_t want = ((int64_t)count + per_block - 1) / per_block;
+  const int64_t want = ((int64_t)count + Cl::kPairsPerBlock - 1) / Cl::kPairsPerBlock;
   const int grid = (int)std::min<int64_t>(want, (int64_t)resident * ctx->num_sms);
-  if constexpr (kSeg)
-    k_bwa_seg<G><<<grid, threads, 0, stream>>>(a, cls, off, count);
+  if constexpr (Cl::kSeg)
+    k_bwa_seg<C><<<grid, Cl::kThreads, 0, stream>>>(a, off, count);
   else
-    k_bwa_cta<G><<<grid, threads, 0, stream>>>(a, cls, off, count);
+    k_bwa_cta<C><<<grid, Cl::kThreads, dyn, stream>>>(a, off, count);
   return cudaGetLastError();
 }
 
 cudaError_t launch_bwa_class(xt_ctx* ctx, const BwaArgs& a, int cls, int32_t off, int32_t count,
                              cudaStream_t stream) {
   switch (cls) {
-    case 0: return launch_class<4>(ctx, a, cls, off, count, stream);
-    case 1: return launch_class<8>(ctx, a, cls, off, count, stream);
-    case 2: return launch_class<16>(ctx, a, cls, off, count, stream);
-    case 3: return launch_class<32>(ctx, a, cls, off, count, stream);
-    case 4: return launch_class<64>(ctx, a, cls, off, count, stream);
-    case 5: return launch_class<128>(ctx, a, cls, off, count, stream);
-    case 6: return launch_class<256>(ctx, a, cls, off, count, stream);
-    case 7: return launch_class<512>(ctx, a, cls, off, count, stream);
+    case 0: return launch_class<0>(ctx, a, off, count, stream);
+    case 1: return launch_class<1>(ctx, a, off, count, stream);
+    case 2: return launch_class<2>(ctx, a, off, count, stream);
+    case 3: return launch_class<3>(ctx, a, off, count, stream);
+    case 4: return launch_class<4>(ctx, a, off, count, stream);
+    case 5: return launch_class<5>(ctx, a, off, count, stream);
+    case 6: return launch_class<6>(ctx, a, off, count, stream);
+    case 7: return launch_class<7>(ctx, a, off, count, stream);
     default: return cudaErrorInvalidValue;
   }
 }
