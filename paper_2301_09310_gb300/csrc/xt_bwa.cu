@@ -49,6 +49,12 @@ constexpr int kBwaClasses = 8;               // G*K = 64 << class columns
 constexpr int kBwaWarpThreads = 128;         // CTA size of the warp-segment classes
 constexpr int32_t kBwaNeg = -(1 << 29);      // below any reachable value
 constexpr uint8_t kBwaDone = 0xff;           // pair finished in classify
+// Within a class pairs go longest query first, in buckets of query length
+// (capped): the groups sharing a warp then extend pairs of like length, whose
+// rows are of like width, and the longest pairs do not start last.
+constexpr int kBwaLenBuckets = 1024;
+constexpr int kBwaScanThreads = 1024;
+static_assert(kBwaLenBuckets * kBwaClasses % kBwaScanThreads == 0, "scan tiling");
 
 static_assert((64 << (kBwaClasses - 1)) == XT_BWA_MAX_WIDTH, "class range must end at the limit");
 
@@ -72,15 +78,18 @@ struct BwaArgs {
   int64_t* cells;
   BwaScore sc;
   uint8_t* pclass;   // [n]
-  int32_t* order;    // [n] pairs grouped by class
-  int32_t* counts;   // [kBwaClasses]
-  int32_t* cursor;   // [kBwaClasses]
+  int32_t* order;    // [n] pairs by class, then by query length (longest first)
+  int32_t* slots;    // [kBwaClasses * kBwaLenBuckets] pairs per (class, length), then positions
+  int32_t* counts;   // [kBwaClasses] pairs per class
   int32_t* heads;    // [kBwaClasses] next pair of each class's persistent kernel
 };
 
-struct ClassOffsets {
-  int32_t off[kBwaClasses];
-};
+// Slot of a pair of class c and query length ql: classes in order, longer
+// queries first within a class.
+__device__ __forceinline__ int32_t bwa_slot(int c, int32_t ql) {
+  const int32_t b = ql < kBwaLenBuckets - 1 ? ql : kBwaLenBuckets - 1;
+  return c * kBwaLenBuckets + (kBwaLenBuckets - 1 - b);
+}
 
 // The narrowed band half-width of a pair with query length qlen.
 __host__ __device__ inline int32_t bwa_band(const BwaScore& s, int32_t qlen) {
@@ -105,11 +114,8 @@ __device__ __forceinline__ void put_result(const BwaArgs& a, int32_t k, int32_t 
 
 // ---------------------------------------------------------------- classify
 // Checks every pair, finishes the degenerate and invalid ones, and counts the
-// rest per group-size class (block-aggregated atomics).
+// rest per (class, query length) slot.
 __global__ void k_bwa_classify(BwaArgs a) {
-  __shared__ int32_t s_cnt[kBwaClasses];
-  if (threadIdx.x < kBwaClasses) s_cnt[threadIdx.x] = 0;
-  __syncthreads();
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < a.n;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int32_t ql = a.q_len[k], tl = a.t_len[k], h0 = a.h0[k];
@@ -134,34 +140,57 @@ __global__ void k_bwa_classify(BwaArgs a) {
       int c = 0;
       while ((64 << c) < width) ++c;
       cls = (uint8_t)c;
-      atomicAdd(&s_cnt[c], 1);
+      atomicAdd(&a.slots[bwa_slot(c, ql)], 1);
     }
     a.pclass[k] = cls;
   }
-  __syncthreads();
-  if (threadIdx.x < kBwaClasses && s_cnt[threadIdx.x] > 0)
-    atomicAdd(&a.counts[threadIdx.x], s_cnt[threadIdx.x]);
 }
 
-// Pairs grouped by class: a block reserves its pairs' positions with one
-// atomic per class, then places them.
-__global__ void k_bwa_scatter(BwaArgs a, ClassOffsets co) {
-  __shared__ int32_t s_cnt[kBwaClasses];
-  __shared__ int32_t s_base[kBwaClasses];
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.n;
-       base += (int64_t)gridDim.x * blockDim.x) {
-    if (threadIdx.x < kBwaClasses) s_cnt[threadIdx.x] = 0;
-    __syncthreads();
-    const int64_t k = base + threadIdx.x;
-    const int c = k < a.n ? a.pclass[k] : kBwaDone;
-    int32_t rank = 0;
-    if (c != kBwaDone) rank = atomicAdd(&s_cnt[c], 1);
-    __syncthreads();
-    if (threadIdx.x < kBwaClasses && s_cnt[threadIdx.x] > 0)
-      s_base[threadIdx.x] = atomicAdd(&a.cursor[threadIdx.x], s_cnt[threadIdx.x]);
-    __syncthreads();
-    if (c != kBwaDone) a.order[co.off[c] + s_base[c] + rank] = (int32_t)k;
-    __syncthreads();
+// One block: slot counts to first positions (exclusive scan in slot order)
+// and the pairs per class.
+__global__ void __launch_bounds__(kBwaScanThreads) k_bwa_scan(BwaArgs a) {
+  constexpr int kPer = kBwaClasses * kBwaLenBuckets / kBwaScanThreads;
+  constexpr int kPerClass = kBwaLenBuckets / kPer;  // threads per class
+  __shared__ int32_t s_warp[kBwaScanThreads / 32];
+  __shared__ int32_t s_class[kBwaClasses];
+  const int tid = threadIdx.x;
+  int32_t v[kPer];
+  int32_t sum = 0;
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    v[u] = a.slots[tid * kPer + u];
+    sum += v[u];
+  }
+  if (tid < kBwaClasses) s_class[tid] = 0;
+  // inclusive scan of the thread sums
+  int32_t inc = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if ((tid & 31) >= o) inc += t;
+  }
+  if ((tid & 31) == 31) s_warp[tid >> 5] = inc;
+  __syncthreads();
+  int32_t before = inc - sum;
+  for (int u = 0; u < (tid >> 5); ++u) before += s_warp[u];
+  atomicAdd(&s_class[tid / kPerClass], sum);
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    a.slots[tid * kPer + u] = before;
+    before += v[u];
+  }
+  __syncthreads();
+  if (tid < kBwaClasses) a.counts[tid] = s_class[tid];
+}
+
+// Each pair takes the next position of its slot.
+__global__ void k_bwa_scatter(BwaArgs a) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < a.n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int c = a.pclass[k];
+    if (c == kBwaDone) continue;
+    const int32_t pos = atomicAdd(&a.slots[bwa_slot(c, a.q_len[k])], 1);
+    if (pos >= 0 && pos < a.n) a.order[pos] = (int32_t)k;
   }
 }
 
@@ -602,8 +631,9 @@ extern "C" xt_status xt_extend_batch_bwa(xt_ctx* ctx, const uint8_t* q_seq, int6
   const size_t n = (size_t)n_pairs;
   const size_t o_cls = 0;
   const size_t o_order = align256(o_cls + n);
-  const size_t o_cnt = align256(o_order + 4 * n);
-  const size_t bytes = align256(o_cnt + 3 * 4 * kBwaClasses);
+  const size_t o_slots = align256(o_order + 4 * n);
+  const size_t n_ctr = (size_t)kBwaClasses * kBwaLenBuckets + 2 * kBwaClasses;
+  const size_t bytes = align256(o_slots + 4 * n_ctr);
   s = ctx_alloc(ctx, &ctx->bwa_ws, &ctx->bwa_ws_bytes, bytes);
   if (s != XT_OK) return s;
   char* ws = static_cast<char*>(ctx->bwa_ws);
@@ -619,15 +649,19 @@ extern "C" xt_status xt_extend_batch_bwa(xt_ctx* ctx, const uint8_t* q_seq, int6
   a.sc.zdrop = scr->zdrop; a.sc.end_bonus = scr->end_bonus;
   a.pclass = reinterpret_cast<uint8_t*>(ws + o_cls);
   a.order = reinterpret_cast<int32_t*>(ws + o_order);
-  a.counts = reinterpret_cast<int32_t*>(ws + o_cnt);
-  a.cursor = a.counts + kBwaClasses;
-  a.heads = a.cursor + kBwaClasses;
+  a.slots = reinterpret_cast<int32_t*>(ws + o_slots);
+  a.counts = a.slots + kBwaClasses * kBwaLenBuckets;
+  a.heads = a.counts + kBwaClasses;
   const int threads = 256;
   const int grid = (int)std::min<int64_t>(((int64_t)n_pairs + threads - 1) / threads,
                                           (int64_t)ctx->num_sms * 8);
-  e = cudaMemsetAsync(a.counts, 0, 3 * 4 * kBwaClasses, st);
+  e = cudaMemsetAsync(a.slots, 0, 4 * n_ctr, st);
   if (e == cudaSuccess) {
     k_bwa_classify<<<grid, threads, 0, st>>>(a);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    k_bwa_scan<<<1, kBwaScanThreads, 0, st>>>(a);
     e = cudaGetLastError();
   }
   // the class sizes come back to size the launches
@@ -637,20 +671,20 @@ extern "C" xt_status xt_extend_batch_bwa(xt_ctx* ctx, const uint8_t* q_seq, int6
   if (e == cudaSuccess) e = cudaEventRecord(ctx->seg_ev, st);
   if (e == cudaSuccess) e = cudaEventSynchronize(ctx->seg_ev);
   if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "BWA classify");
-  ClassOffsets co;
+  int32_t off[kBwaClasses];
   int32_t total = 0;
   int32_t cnt[kBwaClasses];
   for (int c = 0; c < kBwaClasses; ++c) {
     cnt[c] = cnt_host[c];
-    co.off[c] = total;
+    off[c] = total;
     total += cnt[c];
   }
   if (total == 0) return XT_OK;
-  k_bwa_scatter<<<grid, threads, 0, st>>>(a, co);
+  k_bwa_scatter<<<grid, threads, 0, st>>>(a);
   e = cudaGetLastError();
   // widest groups first: they hold the longest rows
   for (int c = kBwaClasses - 1; c >= 0 && e == cudaSuccess; --c)
-    if (cnt[c] > 0) e = launch_bwa_class(ctx, a, c, co.off[c], cnt[c], st);
+    if (cnt[c] > 0) e = launch_bwa_class(ctx, a, c, off[c], cnt[c], st);
   if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "BWA extension");
   ctx->calls++;
   return XT_OK;
