@@ -54,6 +54,10 @@ constexpr uint8_t kBwaDone = 0xff;           // pair finished in classify
 // rows are of like width, and the longest pairs do not start last.
 constexpr int kBwaLenBuckets = 1024;
 constexpr int kBwaScanThreads = 1024;
+// A row buffer element's y word: the column's query code above F.
+constexpr int kCodeShift = 28;
+constexpr uint32_t kFMask = (1u << kCodeShift) - 1u;
+static_assert((int64_t)XT_MAX_H0 + (int64_t)XT_MAX_LEN * 127 < (1ll << kCodeShift), "F fits below the code");
 static_assert(kBwaLenBuckets * kBwaClasses % kBwaScanThreads == 0, "scan tiling");
 
 static_assert((64 << (kBwaClasses - 1)) == XT_BWA_MAX_WIDTH, "class range must end at the limit");
@@ -340,13 +344,14 @@ __device__ __forceinline__ void score_row(uint32_t ti, uint32_t mism4, uint32_t 
 // lane l takes the k = ceil((end - beg) / G) consecutive columns from
 // beg + l*k (fewer in the last lanes).  The row above lives in the group's
 // buffer of G*K + 2 elements, one per column j of [beg - 1, end]: x = H(i-1, j)
-// and y = F(i, j) << 4 | query code of column j, at index j - o(i-1) with the
+// and y = query code of column j << 28 | F(i, j), at index j - o(i-1) with the
 // origin o(r) = max(-1, r - w' - 1).  The origin moves by 0 or 1 column a
 // row, so a row's reads (x of column j-1, y of column j) and its writes (column
 // j at index j - o(i)) touch the same window; a barrier of the group separates
 // the row's reads from its writes.  Two extra elements per row hold the
 // boundary: column beg-1 (x = H of column -1 for the next row: the deletion
-// run from the seed, else 0) and column end (y = 0 | its query code).
+// run from the seed, else 0) and column end (y = its query code << 28 | 0).
+// F and H stay below 2^28: H <= h0 + qlen * match <= 2^20 + 2^20 * 127.
 template <int G, int K>
 __device__ __forceinline__ void bwa_pair(const BwaArgs& a, const Group<G>& g, int2* buf,
                                          int32_t k) {
@@ -364,6 +369,7 @@ __device__ __forceinline__ void bwa_pair(const BwaArgs& a, const Group<G>& g, in
   // row -1 (origin -1): the seed at column -1, the insertion run from it
   // inside the band, no deletion state; each element carries its column's code
   int32_t end = min(qlen, w + 1);
+#pragma unroll 4
   for (int32_t idx = lane; idx < end + 2; idx += G) {
     const int32_t j = idx - 1;
     int32_t x = h0;
@@ -371,8 +377,8 @@ __device__ __forceinline__ void bwa_pair(const BwaArgs& a, const Group<G>& g, in
       const int32_t v = h0 - oe_ins - e_ins * j;
       x = (j < qlen && j + 1 <= w && v > 0) ? v : 0;
     }
-    const int32_t c = (j >= 0 && j < qlen) ? (int32_t)clamp_code(q[j]) : 4;
-    buf[idx] = make_int2(x, c);
+    const uint32_t c = (j >= 0 && j < qlen) ? clamp_code(q[j]) : 4u;
+    buf[idx] = make_int2(x, (int32_t)(c << kCodeShift));
   }
   g.sync();
   int32_t beg = 0;
@@ -387,8 +393,11 @@ __device__ __forceinline__ void bwa_pair(const BwaArgs& a, const Group<G>& g, in
     score_row(clamp_code(t_next), mism4, nb, mb, &rp_lo, &rp_hi);
     if (i + 1 < tlen) t_next = t[i + 1];
     // the query code of column end enters with the row's boundary element
-    const int32_t q_end = (lane == G - 1 && end < qlen) ? (int32_t)clamp_code(q[end]) : 4;
-    const int32_t kq = (end - beg + G - 1) / G;  // <= K: end - beg <= min(qlen, 2w'+1)
+    const uint32_t q_end = (lane == G - 1 && end < qlen) ? clamp_code(q[end]) : 4u;
+    // columns per lane: ceil((end - beg) / G) <= K (end - beg <= min(qlen, 2w'+1)),
+    // rounded up to odd where that stays <= K, so that the lanes of a group
+    // read and write distinct shared-memory banks
+    const int32_t kq = min(((end - beg + G - 1) / G) | 1, K);
     const int32_t first = beg + lane * kq;
     const int32_t cnt = max(0, min(kq, end - first));
 
@@ -405,12 +414,12 @@ __device__ __forceinline__ void bwa_pair(const BwaArgs& a, const Group<G>& g, in
         const int2 e = rd[kk + 1];
         const int32_t D = Dn;
         Dn = e.x;
-        const uint32_t code = (uint32_t)e.y & 15u;
-        const int32_t Sb = prmt_s8(rp_lo, rp_hi, code | 0x5550u);
+        const uint32_t y = (uint32_t)e.y;
+        const int32_t Sb = prmt_s8(rp_lo, rp_hi, (y >> kCodeShift) + 0x5550u);
         const int32_t M = D > 0 ? D + Sb - 128 : 0;
-        const int32_t F = e.y >> 4;
+        const int32_t F = (int32_t)(y & kFMask);
         const int32_t Fn = __viaddmax_s32_relu(M, -oe_del, F - e_del);
-        Yn[kk] = (int32_t)(((uint32_t)Fn << 4) | code);
+        Yn[kk] = (int32_t)((y & ~kFMask) | (uint32_t)Fn);
         Hp[kk] = __vimax3_s32(M, Y, F);
         Y = __viaddmax_s32_relu(M, -oe_ins, Y - e_ins);
       }
@@ -439,8 +448,8 @@ __device__ __forceinline__ void bwa_pair(const BwaArgs& a, const Group<G>& g, in
       }
     }
     const int32_t hb = (beg == 0 && i + 1 <= w) ? max(0, h0 - oe_del - e_del * i) : 0;
-    if (lane == 0) buf[beg - 1 - o_row] = make_int2(hb, 4);
-    if (lane == G - 1) buf[end - o_row] = make_int2(0, q_end);
+    if (lane == 0) buf[beg - 1 - o_row] = make_int2(hb, (int32_t)(4u << kCodeShift));
+    if (lane == G - 1) buf[end - o_row] = make_int2(0, (int32_t)(q_end << kCodeShift));
     const int64_t key = g.all_max64(((int64_t)Hl << 32) | (uint32_t)(first + kl));
     const int32_t m = (int32_t)(key >> 32);
     const int32_t mj = (int32_t)(key & 0xffffffff);
