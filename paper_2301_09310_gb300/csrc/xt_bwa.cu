@@ -26,6 +26,7 @@
 // classified by G*K, and each class runs a persistent kernel whose groups take
 // pairs from a counter.
 #include <algorithm>
+#include <climits>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -226,20 +227,38 @@ struct Group<G, true> {
     const int32_t r = __shfl_up_sync(mask, v, 1, G);
     return lane == 0 ? kBwaNeg : r;
   }
-  __device__ __forceinline__ int64_t all_max64(int64_t v) const {
+  // *m = max of v over the group, *at = the largest col among the lanes
+  // holding it.  A whole warp uses the warp-reduction instructions; a warp
+  // segment, whose neighbours in the warp reduce over other masks at the same
+  // time, a shuffle tree (measured faster there).
+  __device__ __forceinline__ void max_last(int32_t v, int32_t col, int32_t* m,
+                                           int32_t* at) const {
+    if constexpr (G == 32) {
+      const int32_t x = __reduce_max_sync(mask, v);
+      *m = x;
+      *at = __reduce_max_sync(mask, v == x ? col : INT32_MIN);
+    } else {
+      int64_t key = ((int64_t)v << 32) | (uint32_t)col;
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) {
-      const int64_t t = __shfl_xor_sync(mask, v, o, G);
-      v = t > v ? t : v;
+      for (int o = G / 2; o > 0; o >>= 1) {
+        const int64_t t = __shfl_xor_sync(mask, key, o, G);
+        key = t > key ? t : key;
+      }
+      *m = (int32_t)(key >> 32);
+      *at = (int32_t)(key & 0xffffffff);
     }
-    return v;
   }
   // (max of a, min of b) over the group
   __device__ __forceinline__ void all_max_min(int32_t* a, int32_t* b) const {
+    if constexpr (G == 32) {
+      *a = __reduce_max_sync(mask, *a);
+      *b = __reduce_min_sync(mask, *b);
+    } else {
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) {
-      *a = max(*a, __shfl_xor_sync(mask, *a, o, G));
-      *b = min(*b, __shfl_xor_sync(mask, *b, o, G));
+      for (int o = G / 2; o > 0; o >>= 1) {
+        *a = max(*a, __shfl_xor_sync(mask, *a, o, G));
+        *b = min(*b, __shfl_xor_sync(mask, *b, o, G));
+      }
     }
   }
   // one lane takes the next pair of the class for the whole group
@@ -299,12 +318,16 @@ struct Group<G, false> {
     for (int u = 1; u < kW; ++u) r = sh->key[u] > r ? sh->key[u] : r;
     return r;
   }
+  // *m = max of v over the group, *at = col of the highest lane holding it
+  __device__ __forceinline__ void max_last(int32_t v, int32_t col, int32_t* m,
+                                           int32_t* at) const {
+    const int64_t key = all_max64(((int64_t)v << 32) | (uint32_t)col);
+    *m = (int32_t)(key >> 32);
+    *at = (int32_t)(key & 0xffffffff);
+  }
   __device__ __forceinline__ void all_max_min(int32_t* a, int32_t* b) const {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      *a = max(*a, __shfl_xor_sync(0xffffffffu, *a, o));
-      *b = min(*b, __shfl_xor_sync(0xffffffffu, *b, o));
-    }
+    *a = __reduce_max_sync(0xffffffffu, *a);
+    *b = __reduce_min_sync(0xffffffffu, *b);
     if (wl == 0) {
       sh->amax[wid] = *a;
       sh->amin[wid] = *b;
@@ -450,9 +473,8 @@ __device__ __forceinline__ void bwa_pair(const BwaArgs& a, const Group<G>& g, in
     const int32_t hb = (beg == 0 && i + 1 <= w) ? max(0, h0 - oe_del - e_del * i) : 0;
     if (lane == 0) buf[beg - 1 - o_row] = make_int2(hb, (int32_t)(4u << kCodeShift));
     if (lane == G - 1) buf[end - o_row] = make_int2(0, (int32_t)(q_end << kCodeShift));
-    const int64_t key = g.all_max64(((int64_t)Hl << 32) | (uint32_t)(first + kl));
-    const int32_t m = (int32_t)(key >> 32);
-    const int32_t mj = (int32_t)(key & 0xffffffff);
+    int32_t m, mj;
+    g.max_last(Hl, first + kl, &m, &mj);
     g.sync();  // the row is stored
     // end-to-end score when the row reaches the last query column
     if (end == qlen) {
