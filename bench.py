@@ -540,7 +540,7 @@ def bwa_leg(b, wl, args, local, stream):
                          "unit": "Tops/s (int-ALU instructions)", "frac": round(achieved / peak, 4),
                          "ops_per_cell": BWA_OPS_PER_CELL},
             "scoring": list(sc.as_tuple()),
-            "kernel": "k_bwa: one pair per group of 4..512 lanes, a row at a time, int32"}
+            "kernel": "k_bwa: one pair per group of 2..256 lanes, a row's live columns at a time, int32"}
 
 
 def e2e_leg(ctx, b, wl, args, dev, stream, world):

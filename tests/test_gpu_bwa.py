@@ -1,6 +1,7 @@
 """The BWA-MEM-compatible extension (xt_extend_batch_bwa) against the CPU
 oracle's variant, field by field and cell count by cell count: every
-group-size class (4 to 512 lanes per pair), the paper-shaped workloads, edge
+width class (64 to 8,192 columns, 2 to 256 lanes per pair), the paper-shaped
+workloads, edge
 cases, the width limit, raw reads."""
 import numpy as np
 import pytest
@@ -69,7 +70,8 @@ def test_workloads_match_oracle(ctx, name, n):
                                  (4096, 3), (6000, 2)])
 def test_every_group_size(ctx, L, n):
     # equal-length unbanded pairs: the row width is qlen, so L picks the class
-    # (4 lanes up to 64 columns ... 512 lanes up to 8192); some pairs ragged
+    # (2 lanes up to 64 columns ... 256 lanes up to 8192; rows as wide as the
+    # class, 32 columns per lane); some pairs ragged
     wl = synth.x2_workload(L, n_pairs=n)
     b = synth.generate(wl)
     b.q_len[::2] = np.maximum(1, b.q_len[::2] - np.arange(b.q_len[::2].size) * 7 % 50)
@@ -78,7 +80,8 @@ def test_every_group_size(ctx, L, n):
 
 
 def test_large_scores_and_row_widths(ctx):
-    # seed scores past 16 bits, and rows of 209..256 columns (16-lane groups)
+    # seed scores past 16 bits, and rows of 209..256 columns (8-lane groups,
+    # up to 32 columns per lane)
     wl = synth.WORKLOADS["c3_mixed"]
     b = synth.generate(wl, n=6000, first=31)
     sc = BwaScoringParams.from_scoring(wl.scoring)
