@@ -1,8 +1,7 @@
 """The BWA-MEM-compatible extension (xt_extend_batch_bwa) against the CPU
-oracle's variant, field by field and cell count by cell count: every
-width class (64 to 8,192 columns, 2 to 256 lanes per pair), the paper-shaped
-workloads, edge
-cases, the width limit, raw reads."""
+oracle's variant, field by field and cell count by cell count: every width
+class (64 to 8,192 columns, 2 to 256 lanes per pair), the paper-shaped
+workloads, edge cases, the width limit, raw reads."""
 import numpy as np
 import pytest
 
