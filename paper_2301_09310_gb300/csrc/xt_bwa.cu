@@ -364,14 +364,14 @@ __device__ __forceinline__ void score_row(uint32_t ti, uint32_t mism4, uint32_t 
 
 // --------------------------------------------------------------- the kernel
 // One pair per group of G lanes.  Row i computes only its columns [beg, end):
-// lane l takes the k = ceil((end - beg) / G) consecutive columns from
-// beg + l*k (fewer in the last lanes).  The row above lives in the group's
-// buffer of G*K + 2 elements, one per column j of [beg - 1, end]: x = H(i-1, j)
-// and y = query code of column j << 28 | F(i, j), at index j - o(i-1) with the
-// origin o(r) = max(-1, r - w' - 1).  The origin moves by 0 or 1 column a
-// row, so a row's reads (x of column j-1, y of column j) and its writes (column
-// j at index j - o(i)) touch the same window; a barrier of the group separates
-// the row's reads from its writes.  Two extra elements per row hold the
+// lane l takes k consecutive columns from beg + l*k (fewer in the last lanes),
+// k = ceil((end - beg) / G) rounded up to odd while <= K.  The row above lives
+// in the group's buffer of G*K + 2 elements, one per column j of [beg - 1,
+// end]: x = H(i-1, j) and y = query code of column j << 28 | F(i, j), at index
+// j - o(i-1) with the origin o(r) = max(-1, r - w' - 1).  The origin moves by
+// 0 or 1 column a row, so a row's reads (x of column j-1, y of column j) and
+// its writes (column j at index j - o(i)) touch the same window; a barrier of
+// the group separates the row's reads from its writes.  Two extra elements per row hold the
 // boundary: column beg-1 (x = H of column -1 for the next row: the deletion
 // run from the seed, else 0) and column end (y = its query code << 28 | 0).
 // F and H stay below 2^28: H <= h0 + qlen * match <= 2^20 + 2^20 * 127.
