@@ -426,8 +426,15 @@ __device__ __forceinline__ void bwa_pair(const BwaArgs& a, const Group<G>& g, in
 
     // pass 1: M, F and H without the insertion carry from earlier lanes;
     // Y is the lane's insertion chain, started from 0
-    int32_t Hp[K], Yn[K];
-    int32_t Y = 0;
+    // The F word of column j goes to the buffer at once: its index in this
+    // row's layout holds the y word of column j (origin unchanged) or of
+    // column j-1 (origin moved), which this lane has read already.  Only the
+    // first column's word waits for the barrier when the origin moved: the
+    // lane before reads column first-1's y word in this pass.
+    const bool moved = o_row != o_up;
+    int2* wr = buf + (first - o_row);
+    int32_t Hp[K];
+    int32_t Y = 0, y_first = 0;
     if (cnt > 0) {
       const int2* rd = buf + (first - 1 - o_up);
       int32_t Dn = rd[0].x;
@@ -442,7 +449,11 @@ __device__ __forceinline__ void bwa_pair(const BwaArgs& a, const Group<G>& g, in
         const int32_t M = D > 0 ? D + Sb - 128 : 0;
         const int32_t F = (int32_t)(y & kFMask);
         const int32_t Fn = __viaddmax_s32_relu(M, -oe_del, F - e_del);
-        Yn[kk] = (int32_t)((y & ~kFMask) | (uint32_t)Fn);
+        const int32_t yn = (int32_t)((y & ~kFMask) | (uint32_t)Fn);
+        if (kk > 0 || !moved)
+          wr[kk].y = yn;
+        else
+          y_first = yn;
         Hp[kk] = __vimax3_s32(M, Y, F);
         Y = __viaddmax_s32_relu(M, -oe_ins, Y - e_ins);
       }
@@ -457,7 +468,7 @@ __device__ __forceinline__ void bwa_pair(const BwaArgs& a, const Group<G>& g, in
     int32_t Hl = -1, kl = 0;
     uint32_t dead = 0;
     if (cnt > 0) {
-      int2* wr = buf + (first - o_row);
+      if (moved) wr[0].y = y_first;
 #pragma unroll
       for (int kk = 0; kk < K; ++kk) {
         if (kk >= cnt) break;
@@ -467,7 +478,7 @@ __device__ __forceinline__ void bwa_pair(const BwaArgs& a, const Group<G>& g, in
         Hl = ge ? H : Hl;
         kl = ge ? kk : kl;
         dead |= H == 0 ? 1u << kk : 0u;
-        wr[kk] = make_int2(H, Yn[kk]);
+        wr[kk].x = H;
       }
     }
     const int32_t hb = (beg == 0 && i + 1 <= w) ? max(0, h0 - oe_del - e_del * i) : 0;
@@ -526,9 +537,11 @@ struct BwaClass {
   static constexpr size_t kSmem = (size_t)kPairsPerBlock * kBufElems * sizeof(int2);
 };
 
-// Four CTAs per SM (128 registers) for the warp-segment classes.
+// Six CTAs per SM for the warp-segment classes (at most 80 registers, no
+// spills; 6 x 33 KB of row buffers): more warps to cover shared-memory and
+// dependency latency.
 template <int C>
-__global__ void __launch_bounds__(kBwaWarpThreads, 4) k_bwa_seg(BwaArgs a, int32_t off,
+__global__ void __launch_bounds__(kBwaWarpThreads, 6) k_bwa_seg(BwaArgs a, int32_t off,
                                                                 int32_t count) {
   using Cl = BwaClass<C>;
   constexpr int G = Cl::G;

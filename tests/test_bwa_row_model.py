@@ -8,8 +8,10 @@ column j) at index j - o(r), o(r) = max(-1, r - w' - 1), with boundary elements
 at columns beg - 1 and end.  This test replays that decomposition lane by lane
 in Python (a model of the indexing, not the CUDA code) and checks it against
 the oracle: every buffer index in range, no element read before it is written,
-each column's query code carried with it, and the oracle's result for several
-group sizes and for odd as well as exact column counts per lane.
+each column's query code carried with it, F words written while the row above is
+still being read landing only on words their own lane has read, and the
+oracle's result for several group sizes and for odd as well as exact column
+counts per lane.
 """
 import random
 
@@ -28,7 +30,7 @@ def score(sc, ti, qc):
     return sc.match if ti == qc else sc.mismatch
 
 
-def extend_by_rows(q, t, h0, sc, G, odd):
+def extend_by_rows(q, t, h0, sc, G, odd, early_f=False):
     """Extend one pair the way the kernel's lanes do; returns the oracle's tuple."""
     qlen, tlen = len(q), len(t)
     w = oracle.bwa_band(sc, qlen)
@@ -70,7 +72,10 @@ def extend_by_rows(q, t, h0, sc, G, odd):
             kq = min(kq | 1, kmax)
         assert kq <= kmax
         lanes = []
-        for lane in range(G):  # pass 1: reads of the row above only
+        shifted = o_row != o_up
+        y_readers = {}  # buffer index -> lane that reads its y word in pass 1
+        early = []      # (lane, index, y) written during pass 1
+        for lane in range(G):  # pass 1: reads of the row above, early F words
             first = beg + lane * kq
             cnt = max(0, min(kq, end - first))
             Y, Hp, Yn = 0, [], []
@@ -78,6 +83,7 @@ def extend_by_rows(q, t, h0, sc, G, odd):
                 Dn = read(first - 1 - o_up)[0]
                 for kk in range(cnt):
                     x, y = read(first + kk - o_up)
+                    y_readers[first + kk - o_up] = lane
                     D, Dn = Dn, x
                     c, F = y >> 28, y & ((1 << 28) - 1)
                     assert c == code(first + kk)
@@ -86,7 +92,16 @@ def extend_by_rows(q, t, h0, sc, G, odd):
                     Yn.append((c << 28) | Fn)
                     Hp.append(max(M, Y, F))
                     Y = max(M - oe_ins, Y - sc.e_ins, 0)
+                    if early_f and (kk > 0 or not shifted):
+                        early.append((lane, first + kk - o_row, Yn[-1]))
             lanes.append((first, cnt, Y, Hp, Yn))
+        # an F word written during pass 1 lands on a y word that only its own
+        # lane reads, and that lane has read it already (an earlier or the
+        # same column); x words are not written before the barrier
+        for lane, idx, y in early:
+            assert y_readers.get(idx, lane) == lane, (i, lane, idx)
+            assert 0 <= idx < len(buf)
+            buf[idx] = (buf[idx][0] if buf[idx] is not None else None, y)
         decay = sc.e_ins * kq
         best_lane = (-1, 0)
         dead = []
@@ -100,6 +115,8 @@ def extend_by_rows(q, t, h0, sc, G, odd):
                 if (H, first + kk) > best_lane:
                     best_lane = (H, first + kk)
                 dm |= (H == 0) << kk
+                if early_f and (kk > 0 or not shifted):
+                    assert buf[first + kk - o_row][1] == Yn[kk]
                 write(first + kk - o_row, (H, Yn[kk]))
             dead.append(dm)
         hb = max(0, h0 - oe_del - sc.e_del * i) if (beg == 0 and i + 1 <= w) else 0
@@ -164,8 +181,10 @@ def test_row_split_matches_oracle(si):
     for _ in range(40):
         q, t, h0 = random_pair(rng)
         want = oracle.extend_one_bwa(np.array(q, np.uint8), np.array(t, np.uint8), h0, sc)
-        for G, odd in ((2, True), (8, True), (3, False), (64, True)):
-            assert extend_by_rows(q, t, h0, sc, G, odd) == want, (si, G, odd, q, t, h0)
+        for G, odd, early_f in ((2, True, False), (8, True, True), (3, False, True),
+                                (64, True, False)):
+            got = extend_by_rows(q, t, h0, sc, G, odd, early_f)
+            assert got == want, (si, G, odd, early_f, q, t, h0)
 
 
 def test_row_split_long_pair_full_width_rows():
