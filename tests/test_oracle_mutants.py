@@ -31,6 +31,10 @@ MUTANTS = {
     "gscore_latest_row": ("if (g > 0 && g > gscore)", "if (g > 0 && g >= gscore)"),
     "zdrop_no_gap_correction": ("int64_t drop = best - m - iabs64(d) * beta;",
                                 "int64_t drop = best - m;"),
+    "zdrop_ties_stop": ("      if (drop > sc->zdrop) break;\n    }\n    int64_t* tmp;",
+                        "      if (drop >= sc->zdrop) break;\n    }\n    int64_t* tmp;"),
+    "zdrop_signed_offset": ("int64_t drop = best - m - iabs64(d) * beta;",
+                            "int64_t drop = best - m - d * beta;"),
     "boundary_row_missing_open": ("int64_t v = max2(0, h0 - alpha - beta * c);",
                                   "int64_t v = max2(0, h0 - beta - beta * c);"),
     "n_scored_as_mismatch": ("if (a >= 4 || b >= 4) return sc->n_score;",
@@ -68,6 +72,7 @@ def pins_fail():
         pins.test_all_mismatch_single_cell_gscore,
         pins.test_boundary_runs_match_enumeration,
         pins.test_path_enumeration_fixes_every_cell,
+        pins.test_path_enumeration_fixes_zdrop,
     ]
     for c in checks:
         try:

@@ -188,9 +188,13 @@ def enumerate_paths(q, t, h0, sc: Scoring):
 
 
 def outputs_from_H(H, q, t, h0, sc):
-    """score/positions/gscore/max_off/cells from an interior H matrix, with
-    z-drop disabled: rows in order, largest column within a row, strictly
-    greater to move the best."""
+    """score/positions/gscore/max_off/cells from an interior H matrix: rows in
+    order, largest column within a row, strictly greater to move the best.
+    With sc.zdrop > 0 a row that does not raise the best ends the extension
+    when best - m - |(i - bi) - (mj - bj)| * beta > zdrop, after that row's
+    gscore update; rows after it count for nothing (Q6).  H is the full
+    matrix, so the cut-off is applied here and nowhere else."""
+    beta = sc.gap_extend
     tl, ql = H.shape
     if ql == 0:
         return (h0, 0, 0, h0, 0, 0, 0), 0
@@ -210,6 +214,10 @@ def outputs_from_H(H, q, t, h0, sc):
         if m > best:
             best, bi, bj = m, i, mj
             max_off = max(max_off, abs(mj - i))
+        elif sc.zdrop > 0:
+            d = (i - bi) - (mj - bj)
+            if best - m - abs(d) * beta > sc.zdrop:
+                break
     cells = sum(len([j for j in range(ql) if abs(i - j) <= sc.w]) for i in range(last_live + 1))
     return (best, bj + 1, bi + 1, g, gtle, max_off, 0), cells
 
@@ -242,6 +250,28 @@ def test_path_enumeration_fixes_every_cell():
         assert tr.result == res, (q, t, h0, sc)
         assert tr.cells == cells, (q, t, h0, sc)
     assert n_nontrivial > 100
+
+
+def test_path_enumeration_fixes_zdrop():
+    """Z-drop pinned independently of the oracle: the enumerated (full) H of
+    each random tiny case, cut off in row order by the rule above, against
+    the oracle run with the same cutoff, on every field and on cells."""
+    rng = random.Random(2302)
+    n_cut = 0
+    for _ in range(400):
+        q, t, h0, sc0 = random_case(rng)
+        H, _, _ = enumerate_paths(q, t, h0, sc0)
+        full, full_cells = outputs_from_H(H, q, t, h0, sc0)
+        for z in (1, 3, 8):
+            sc = Scoring(match=sc0.match, mismatch=sc0.mismatch, gap_open=sc0.gap_open,
+                         gap_extend=sc0.gap_extend, w=sc0.w, zdrop=z, n_score=sc0.n_score)
+            res, cells = oracle.extend_one(q, t, h0, sc)
+            want, want_cells = outputs_from_H(H, q, t, h0, sc)
+            assert res == want, (q, t, h0, sc)
+            assert cells == want_cells, (q, t, h0, sc)
+            n_cut += int((want, want_cells) != (full, full_cells))
+    # the cutoff changed the outputs of a good share of the cases
+    assert n_cut > 50, n_cut
 
 
 def test_boundary_runs_match_enumeration():
@@ -322,7 +352,11 @@ def test_output_ranges():
         assert np.all((cells >= 0) & (cells <= qlen.astype(np.int64) * tlen))
 
 
-def test_wide_band_equals_unbanded():
+def test_band_beyond_every_pair_changes_nothing():
+    """An invariant of the static band (Q5), not a pin: once w exceeds every
+    pair's lengths no cell leaves the band, so any larger w gives the same
+    results.  (The band itself is pinned by path enumeration with w in
+    {0, 1, 2, 3, 10} and by the hand-worked band table.)"""
     rng = random.Random(13)
     qs, ts = batch_of(rng, 200, 40, 20)
     qd, qo, qlen = pack(qs)
