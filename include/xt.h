@@ -384,6 +384,31 @@ xt_status xt_extend_batch_bwa(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_bytes
                               const int32_t* h0, int32_t n_pairs, const xt_bwa_scoring* sc,
                               xt_result* out, int64_t* cells_out, void* stream);
 
+/*
+ * Measurement aid (not part of the method): the throughput of one kind of
+ * integer instruction on `device`, which sets the roofline of the extension
+ * DP (integer arithmetic, no dense contraction).  A probe kernel runs the
+ * instruction in independent chains on every SM (8 chains per thread, a full
+ * SM of warps) and is timed with CUDA events after one warm-up launch; the
+ * best of `reps` launches is returned: *units instructions (thread-level) in
+ * *ms milliseconds.  XT_RATE_MIX alternates a packed 3-way max with a 32-bit
+ * multiply-add, two instructions that issue to different pipes, so it
+ * measures the issue rate.  XT_RATE_CELL_P16 runs the packed cell update of
+ * the one-lane engine on registers (the engine's fast step, 16 cells per step
+ * and thread); *units then counts cells.  Synchronous; allocates a few bytes
+ * of device memory; XT_EINVAL for an unknown op or device.
+ */
+#define XT_RATE_ADD16X2 0      /* add.s16x2 */
+#define XT_RATE_MAX3_16X2 1    /* 3-way packed 16-bit max */
+#define XT_RATE_ADDMAX_16X2 2  /* packed 16-bit add-max with relu */
+#define XT_RATE_PRMT 3         /* byte permute */
+#define XT_RATE_IADD3 4        /* 32-bit three-input add */
+#define XT_RATE_MAX3_32 5      /* 3-way 32-bit max */
+#define XT_RATE_IMAD 6         /* 32-bit multiply-add */
+#define XT_RATE_MIX 7          /* packed 3-way max and multiply-add, alternating */
+#define XT_RATE_CELL_P16 8     /* the packed cell update (cells, not instructions) */
+xt_status xt_int_rate(int device, int op, int reps, int64_t* units, double* ms);
+
 /* Human-readable name of a status code (static storage). */
 const char* xt_status_str(xt_status s);
 
@@ -410,11 +435,16 @@ const char* xt_ctx_last_error(const xt_ctx* ctx);
  *   pair's boundary ring fits in shared memory (w up to about 1900; wider
  *   bands need xt_extend_batch, which can grow a global ring pool).
  * The first call on each device looks up the array's device address once
- * (cudaGetSymbolAddress), so make that first call before any stream capture
- * on that device.  All calls share the one array and it keeps the previous
- * call's contents (the call zeroes what must start at zero): calls whose
- * work overlaps on the GPU (other streams, other host threads) race on it,
- * so order them, e.g. on one stream.
+ * (cudaGetSymbolAddress) and keeps it for the life of the process, so make
+ * that first call before any stream capture on that device.  The address
+ * belongs to the device's primary context: after a cudaDeviceReset of that
+ * device it is no longer valid, so a process that resets a device must not
+ * call this entry point on it again.  All calls share the one array and it
+ * keeps the previous call's contents (the call zeroes what must start at
+ * zero): calls whose work overlaps on the GPU (other streams, other host
+ * threads) race on it, so order them, e.g. on one stream.  The batch
+ * descriptor goes to the device as a kernel parameter, so no host memory of
+ * the call has to outlive it.
  */
 #define XT_STATIC_MAX_PAIRS (1 << 20)
 #define XT_STATIC_SCRATCH_BYTES ((size_t)6 << 20)

@@ -11,6 +11,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import time
 from dataclasses import dataclass
 
 from . import build as _build
@@ -30,8 +31,16 @@ EXPORTED = ("xt_ctx_create", "xt_ctx_destroy", "xt_ctx_sync", "xt_extend_batch",
             "xt_ctx_load_tuning", "xt_ctx_set_bucket_schedule_for",
             "xt_ctx_get_bucket_schedule_for", "xt_extend_batch_begin", "xt_extend_batch_ready",
             "xt_extend_batch_finish", "xt_ctx_set_alphabet", "xt_extend_seeds",
-            "xt_extend_batch_bwa", "xt_bwa_scoring_check")
+            "xt_extend_batch_bwa", "xt_bwa_scoring_check", "xt_int_rate")
 XT_STATIC_MAX_PAIRS = 1 << 20
+# instruction kinds of xt_int_rate (measurement aid)
+XT_RATE_ADD16X2, XT_RATE_MAX3_16X2, XT_RATE_ADDMAX_16X2, XT_RATE_PRMT = 0, 1, 2, 3
+XT_RATE_IADD3, XT_RATE_MAX3_32, XT_RATE_IMAD, XT_RATE_MIX, XT_RATE_CELL_P16 = 4, 5, 6, 7, 8
+RATE_NAMES = {XT_RATE_ADD16X2: "add.s16x2", XT_RATE_MAX3_16X2: "max3.s16x2",
+              XT_RATE_ADDMAX_16X2: "addmax.relu.s16x2", XT_RATE_PRMT: "prmt",
+              XT_RATE_IADD3: "iadd3.s32", XT_RATE_MAX3_32: "max3.s32", XT_RATE_IMAD: "imad.u32",
+              XT_RATE_MIX: "max3.s16x2 + imad.u32 alternating",
+              XT_RATE_CELL_P16: "packed cell update (cells)"}
 
 
 class xt_scoring(ctypes.Structure):
@@ -162,6 +171,9 @@ def load_library(path: str | None = None):
     lib.xt_ctx_last_error.restype = ctypes.c_char_p
     lib.xt_scoring_check.argtypes = [ctypes.POINTER(xt_scoring)]
     lib.xt_scoring_check.restype = ctypes.c_int
+    lib.xt_int_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
+    lib.xt_int_rate.restype = ctypes.c_int
     lib.xt_now_ns.argtypes = []
     lib.xt_now_ns.restype = ctypes.c_int64
     lib.xt_serve_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(xt_serve_config)]
@@ -258,6 +270,14 @@ def xt_ctx_set_alphabet(ctx: int, alphabet: int) -> int:
 
 def xt_ctx_set_streams(ctx: int, branches: int) -> int:
     return load_library().xt_ctx_set_streams(ctypes.c_void_p(ctx), int(branches))
+
+
+def xt_int_rate(device: int, op: int, reps: int = 3):
+    """(status, units, ms): one instruction kind's throughput probe."""
+    units, ms = ctypes.c_int64(0), ctypes.c_double(0.0)
+    s = load_library().xt_int_rate(int(device), int(op), int(reps), ctypes.byref(units),
+                                   ctypes.byref(ms))
+    return s, units.value, ms.value
 
 
 def xt_ctx_set_timing(ctx: int, enable: bool) -> int:
@@ -682,11 +702,16 @@ class Server:
         out = np.empty((n, 7), np.int32)
         cells = np.empty(n, np.int64) if want_cells else None
         p = lambda a: a.ctypes.data if a is not None and a.size else 0  # noqa: E731
+        backoff = 50e-6
         while True:
             s, ticket = xt_serve_submit(self.handle, p(arrs[0]), arrs[0].size, p(arrs[1]),
                                         p(arrs[2]), p(arrs[3]), arrs[3].size, p(arrs[4]),
                                         p(arrs[5]), p(arrs[6]), n, scoring, p(out), p(cells))
             if s == XT_EBUSY and retry_busy:
+                # the queue drains as batches form; sleeping leaves the host
+                # cores to the server's gather threads
+                time.sleep(backoff)
+                backoff = min(2 * backoff, 2e-3)
                 continue
             if s != XT_OK:
                 raise XtError(s, "xt_serve_submit")

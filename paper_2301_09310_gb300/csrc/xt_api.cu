@@ -1295,7 +1295,8 @@ std::mutex g_static_mu;
 void* g_static_ptr[kStaticMaxDevices] = {};
 
 // Device address of the scratch array on the current device (looked up on
-// the first call for that device).
+// the first call for that device and kept for the life of the process; a
+// cudaDeviceReset of that device invalidates it, see include/xt.h).
 cudaError_t static_scratch(int device, void** ptr) {
   std::lock_guard<std::mutex> lk(g_static_mu);
   if (!g_static_ptr[device]) {
@@ -1373,13 +1374,13 @@ extern "C" xt_status xt_extend_batch_static(const uint8_t* q_seq, int64_t q_byte
   b.q_seq = q_seq; b.t_seq = t_seq; b.q_off = q_off; b.t_off = t_off; b.q_len = q_len;
   b.t_len = t_len; b.h0 = h0; b.q_bytes = q_bytes; b.t_bytes = t_bytes; b.n = n_pairs; b.out = out;
   b.cells = cells_out;
-  // the descriptor goes to the device copy from this stack frame; a copy
-  // from pageable memory is staged before the call returns
-  cudaError_t e0 = cudaMemcpyAsync(desc, &b, sizeof(Batch), cudaMemcpyHostToDevice, st);
-  if (e0 != cudaSuccess) return XT_ECUDA;
+  // the descriptor travels to its device slot as a kernel parameter: no
+  // host buffer has to outlive the call, and no copy waits behind bulk
+  // copies that other streams queued on the copy engine
+  cudaError_t e = launch_store_desc(desc, b, st);
   // counters and queue heads start at zero on every call; the bucket flags
   // are rewritten; everything else is written before it is read
-  cudaError_t e = cudaMemsetAsync(w.counts, 0, 4 * (size_t)kNumBuckets, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.counts, 0, 4 * (size_t)kNumBuckets, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(w.heads, 0, 4 * (size_t)kMaxLaunches, st);
   if (e == cudaSuccess) e = launch_classify(desc, n_pairs, sc, scr->match, pl.jf, w, st);
   if (e == cudaSuccess) e = launch_order(desc, n_pairs, w, st);

@@ -1,6 +1,7 @@
 // xt_kernels.cu -- classify/bucket, ordering, persistent queue kernels and the
 // plain one-pair-per-block kernel.
 #include <cstdio>
+#include <mutex>
 
 #include "xt_engine.cuh"
 #include "xt_kernels.cuh"
@@ -506,6 +507,30 @@ cudaError_t launch_seed_right_h0(int32_t n, const int32_t* h0, const xt_result* 
 // could pass the 48 KB a kernel gets without opting in.
 constexpr size_t kStaticSmemMax = 1024;
 
+// The dynamic shared-memory limit of a kernel is one attribute per (kernel,
+// device) for the whole process, and calls of several contexts (or a context
+// call and an allocation-free call) may launch the same kernel from several
+// host threads at once.  The limit is therefore only ever raised, under a
+// lock, never set back to a smaller launch's size: it is a cap, and each
+// launch's occupancy still follows its own dynamic size.
+constexpr int kAttrDevices = 64;
+
+template <typename K>
+cudaError_t raise_smem_limit(K kern, size_t smem) {
+  static std::mutex mu;
+  static int limit[kAttrDevices] = {};
+  if (smem + kStaticSmemMax <= 48 * 1024) return cudaSuccess;  // the default limit covers it
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  const bool tracked = dev >= 0 && dev < kAttrDevices;
+  if (tracked && limit[dev] >= (int)smem) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && tracked) limit[dev] = (int)smem;
+  return e;
+}
+
 cudaError_t launch_classify(const Batch* bd, int32_t n_cap, const Score& sc, int32_t match,
                             const JFlags& jf, const Work& w, cudaStream_t stream) {
   if (n_cap == 0) return cudaSuccess;
@@ -534,11 +559,8 @@ static cudaError_t launch_queue_t(const Batch* b, const Score& sc, const Work& w
                                   int head_id, int2* gring, cudaStream_t stream) {
   const size_t smem = L.global_ring ? 0 : queue_smem_bytes(P, L.rs_log2);
   auto kern = k_queue<P, R, WIDE>;
-  if (smem + kStaticSmemMax > 48 * 1024) {  // the default limit covers static + dynamic
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  cudaError_t e = raise_smem_limit(kern, smem);
+  if (e != cudaSuccess) return e;
   kern<<<L.grid, kQueueThreads, smem, stream>>>(b, sc, w, L.cls, L.j_lo, L.j_hi, head_id,
                                                 L.rs_log2, L.global_ring ? gring : nullptr,
                                                 L.slab);
@@ -577,11 +599,8 @@ static cudaError_t launch_lane_t(const Batch* b, const Score& sc, const Work& w,
   const size_t smem = (GRING ? 0 : kLaneThreads * lane_ring_bytes(L.cls, L.rs_log2)) +
                       (QSTAGE ? lane_stage_bytes(L.j_hi) : 0);
   auto kern = k_lane<R, PACKED, GRING, QSTAGE>;
-  if (smem + kStaticSmemMax > 48 * 1024) {  // the default limit covers static + dynamic
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  cudaError_t e = raise_smem_limit(kern, smem);
+  if (e != cudaSuccess) return e;
   kern<<<L.grid, kLaneThreads, smem, stream>>>(b, sc, w, L.cls, L.j_lo, L.j_hi, head_id,
                                                L.rs_log2, gring, L.mparam, L.j_hi);
   return cudaGetLastError();
@@ -619,11 +638,8 @@ cudaError_t launch_plain(const Batch* b, int32_t n_cap, const Score& sc, const W
                          int rs_log2, cudaStream_t stream) {
   if (n_cap == 0) return cudaSuccess;
   const size_t smem = ((size_t)1 << rs_log2) * sizeof(int2);
-  if (smem + kStaticSmemMax > 48 * 1024) {  // the default limit covers static + dynamic
-    cudaError_t e = cudaFuncSetAttribute(k_plain, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  cudaError_t e = raise_smem_limit(k_plain, smem);
+  if (e != cudaSuccess) return e;
   k_plain<<<n_cap, 32, smem, stream>>>(b, sc, w, rs_log2);
   return cudaGetLastError();
 }

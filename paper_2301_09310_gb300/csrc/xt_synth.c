@@ -5,7 +5,7 @@
  * is shared by the tests, the bench and the oracle runs as a source of inputs.
  *
  * The paper measures on BWA-MEM seeds from GRCh38 with Illumina MiSeq reads
- * (SRR835433, 250 bp) and PacBio reads (SRP091981, ~2 kbp) (Sec. V-C), and on
+ * (SRR835433, 250 bp) and PacBio reads (SRP091981, ~2 kbp) (Sec. V-D), and on
  * equal-length synthetic reads from a wgsim-like simulator (Sec. V-B).  Neither
  * the genome nor the reads exist here; this generator stands in for them with
  * the same shape: a reference window of uniform A/C/G/T (a small fraction N),

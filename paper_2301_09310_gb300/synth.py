@@ -1,7 +1,7 @@
 """Seeded synthetic seed-extension workloads (input generation only).
 
 Stands in for the paper's BWA-MEM seeds on GRCh38 with MiSeq 250 bp and
-PacBio ~2 kbp reads (Sec. V-C) and for its wgsim-like equal-length reads
+PacBio ~2 kbp reads (Sec. V-D) and for its wgsim-like equal-length reads
 (Sec. V-B), which are not available here.  Shapes follow the five workload
 presets below; the C generator (csrc/xt_synth.c) draws every base from a
 counter-based SplitMix64 keyed by (seed, pair index), so results are the same

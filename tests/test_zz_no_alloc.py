@@ -87,3 +87,33 @@ def test_static_refuses_beyond_limits():
     s, out, _ = _static_call(args, b.n, ScoringParams(), stream)
     torch.cuda.synchronize()
     assert s == xt.XT_OK and int(out[:, 6].max().item()) <= 1
+
+
+def test_static_at_its_pair_limit():
+    """XT_STATIC_MAX_PAIRS short pairs: the carved tables come closest to the
+    end of the fixed array; results equal xt_extend_batch's."""
+    import torch
+    import paper_2301_09310_gb300 as xt
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    n = xt.XT_STATIC_MAX_PAIRS
+    wl = synth.WORKLOADS["c2_short"]
+    b = synth.generate(wl, n=n)
+    sc = wl.scoring
+    args = to_dev(b, dev)
+    ctx = xt.Context(0)
+    try:
+        want_out, want_cells = ctx.extend(*args, sc)
+        torch.cuda.synchronize()
+        want_out, want_cells = want_out.cpu().numpy(), want_cells.cpu().numpy()
+    finally:
+        ctx.close()
+    for k in range(2):
+        s, out, cells = _static_call(args, n, sc, stream)
+        assert s == xt.XT_OK, xt.xt_status_str(s)
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), want_out), f"call {k}: results differ"
+        assert np.array_equal(cells.cpu().numpy(), want_cells), f"call {k}: cells differ"
