@@ -10,9 +10,10 @@ Prints one JSON line: GCUPS (useful in-band cells per second, cells counted
 by the oracle's definition and returned by the kernels), extensions/s, the
 plain one-pair-per-block kernel on the same batch, the end-to-end figure
 through the host-buffer API (H2D of inputs and D2H of results inside the
-timed region), the roofline of the extension kernels against the integer-ALU
-issue peak, SM clocks sampled during the timed region, and the CPU oracle
-timed on the host cores on a bounded sample.
+timed region), the roofline of the extension kernels against the integer
+ALU pipe's and the issue rate measured on this GPU by instruction probes,
+SM clocks sampled during the timed region, and the CPU oracle timed on the
+host cores on a bounded sample.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c3_mixed]
   python bench.py --impl reference ...   # the CPU oracle on the same workload
@@ -36,17 +37,23 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "seed-extension GCUPS & extensions/s (bit-exact), batched vs plain; p50/p99 latency"
-# Integer-ALU issue peak: 152 SMs x 128 int32 lanes per SM per clock (measured
-# issue-bound rate of IADD/IMNMX/PRMT/DPX ops on this GPU) x 2070 MHz max SM clock.
-SMS, LANES, MAX_MHZ = 152, 128, 2070.0
-# BWA-MEM-compatible cell, 32-bit: S, M (add, select), F and E (add-max each), H (3-way max), row key
-BWA_OPS_PER_CELL = 10
-# Algorithmic instructions per cell with the fused DPX forms native on sm_103a:
-# S (byte permute), anchored diagonal (multiply + add-min), E and F (add-max
-# with relu each), H (3-way max), H - alpha, row key (multiply-add + max): 9-10
-# in 32-bit; the packed 16-bit form does two cells per instruction.
-OPS_PER_CELL_INT32 = 10
-OPS_PER_CELL_PACKED = 5
+# Fallback only (no measured rate): 152 SMs, 2070 MHz maximum SM clock.
+SMS, MAX_MHZ = 152, 2070.0
+# Algorithmic instructions of one cell update (one 32-bit cell, or two cells
+# in the packed 16-bit form), with the fused DPX forms native on sm_103a:
+# on the integer ALU pipe S (byte permute), the anchored diagonal's add-min,
+# E and F (add-max with relu each), H (3-way max), H - alpha and the row key's
+# max: 7; on the multiply-add pipe the anchoring multiplier D * 2^k and the
+# row key H * 64 + step (H * 65536 + j in 32-bit): 2.
+ALU_OPS_PER_UPDATE, MAD_OPS_PER_UPDATE = 7, 2
+OPS_PER_UPDATE = ALU_OPS_PER_UPDATE + MAD_OPS_PER_UPDATE
+# BWA-MEM-compatible cell, 32-bit: S, M (add, select), E and F (M minus the
+# opening penalty, then add-max each), H (3-way max), the row key's max: 9 on
+# the ALU pipe, and the key's multiply-add on the other: 10
+BWA_ALU_OPS_PER_CELL, BWA_OPS_PER_CELL = 9, 10
+# instruction probes whose rate is the integer ALU pipe's (the kinds the
+# cell update issues there)
+ALU_PROBES = ("add.s16x2", "max3.s16x2", "addmax.relu.s16x2", "prmt", "max3.s32")
 LANE_MAX_QLEN = 510  # one-lane (packed-capable) buckets: qlen + 2 <= 2^9
 WORKLOAD_TEXT = {
     "c1_tiny": "1,000 pairs, 100 bp queries, 116 bp targets, 2% sub / 0.2% indel",
@@ -77,7 +84,9 @@ def parse_args():
                     help="skip the BWA-MEM-compatible extension leg")
     ap.add_argument("--no-x2", action="store_true",
                     help="skip the equal-length 5,000-pair calls of the paper's kernel comparison")
-    ap.add_argument("--serve-pairs", type=int, default=4_000_000,
+    ap.add_argument("--no-c4", action="store_true",
+                    help="skip the 250,000 long pairs of c4_long (w = 500, z-drop 400)")
+    ap.add_argument("--serve-pairs", type=int, default=10_000_000,
                     help="pairs of the c5 stream per offered-load level")
     ap.add_argument("--tune", choices=["auto", "off"], default="auto",
                     help="auto: autotune the workload's length buckets before warm-up")
@@ -185,11 +194,11 @@ def aggregate(world, units_local: float, seconds_local: float):
     return total, slowest, total / slowest
 
 
-def algorithmic_ops(b, cells, sc):
-    """Instructions the extension DP needs for this batch: cells of pairs that
+def cell_updates(b, cells, sc):
+    """Cell updates the extension DP needs for this batch: cells of pairs that
     the packed 16-bit class takes (score bound B = h0 + match*min(qlen,tlen)
     with (B+1)*2^k and B*64+63 within int16, query within the one-lane
-    buckets) at OPS_PER_CELL_PACKED, the rest at OPS_PER_CELL_INT32."""
+    buckets) count half (two cells per update), the rest one each."""
     m = sc.match
     k = 0
     while (1 << k) < m + 1:
@@ -197,8 +206,65 @@ def algorithmic_ops(b, cells, sc):
     bound = b.h0.astype(np.int64) + m * np.minimum(b.q_len, b.t_len).astype(np.int64)
     packed = ((bound + 1) << k <= 32767) & (bound * 64 + 63 <= 32767) & (b.q_len <= LANE_MAX_QLEN)
     c = cells.astype(np.float64)
-    ops = OPS_PER_CELL_PACKED * c[packed].sum() + OPS_PER_CELL_INT32 * c[~packed].sum()
-    return float(ops), float(c[packed].sum() / max(c.sum(), 1.0))
+    updates = 0.5 * c[packed].sum() + c[~packed].sum()
+    return float(updates), float(c[packed].sum() / max(c.sum(), 1.0))
+
+
+def measure_int_rates(local):
+    """Throughput of each integer instruction kind of the cell update on this
+    GPU (xt_int_rate probes, CUDA events), with the SM clock sampled while
+    they run: thread-instructions per SM per clock for each kind."""
+    import paper_2301_09310_gb300 as xt
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    raw = {}
+    for op, name in xt.RATE_NAMES.items():
+        s, units, ms = xt.xt_int_rate(local, op, 5)
+        if s != xt.XT_OK:
+            raise RuntimeError(f"xt_int_rate({name}): {xt.xt_status_str(s)}")
+        raw[name] = (units, ms)
+    clocks = sampler.stop()
+    mhz = clocks["sm_mhz"] if clocks else MAX_MHZ
+    sms = _sm_count(local)
+    per_clk = {k: u / (ms / 1e3) / sms / (mhz * 1e6) for k, (u, ms) in raw.items()}
+    return {"per_sm_per_clock": {k: round(v, 2) for k, v in per_clk.items()},
+            "ms": {k: round(ms, 4) for k, (_, ms) in raw.items()},
+            "sm_mhz": mhz, "sms": sms, "clocks": clocks,
+            "alu_pipe": max(per_clk[k] for k in ALU_PROBES),
+            "mad_pipe": per_clk["imad.u32"], "issue": per_clk["max3.s16x2 + imad.u32 alternating"],
+            "cell_update_cells": per_clk["packed cell update (cells)"]}
+
+
+def _sm_count(local):
+    import torch
+    return torch.cuda.get_device_properties(local).multi_processor_count
+
+
+def int_roofline(updates, kernel_ms, rates, mhz, alu_ops=ALU_OPS_PER_UPDATE,
+                 all_ops=OPS_PER_UPDATE):
+    """Roofline of integer DP kernels against the measured pipe rates at the
+    SM clock the kernels ran at: the headline fraction is the algorithmic
+    ALU-pipe instructions per second over the ALU pipe's measured rate (the
+    pipe that binds the cell update's mix); the issue fraction counts every
+    algorithmic instruction against the measured issue rate."""
+    sec = kernel_ms / 1e3
+    clk = mhz * 1e6 * rates["sms"]
+    alu_peak = rates["alu_pipe"] * clk / 1e12
+    issue_peak = rates["issue"] * clk / 1e12
+    alu_ach = updates * alu_ops / sec / 1e12
+    all_ach = updates * all_ops / sec / 1e12
+    return {"bound": "alu", "unit": "Tops/s (int-ALU-pipe instructions)",
+            "achieved": round(alu_ach, 3), "peak": round(alu_peak, 3),
+            "frac": round(alu_ach / alu_peak, 4),
+            "peak_basis": (f"measured: ALU-pipe probe {rates['alu_pipe']:.2f} thread-instr/SM/clk "
+                           f"x {rates['sms']} SMs x {mhz:.0f} MHz (median SM clock of the timed "
+                           "region), of measured"),
+            "issue": {"achieved": round(all_ach, 3), "peak": round(issue_peak, 3),
+                      "frac": round(all_ach / issue_peak, 4),
+                      "basis": f"measured issue probe {rates['issue']:.2f} thread-instr/SM/clk "
+                               "(ALU and multiply-add pipes alternating), every algorithmic "
+                               "instruction counted, of measured"}}
 
 
 # the files that define the extension kernels' device code
@@ -370,11 +436,12 @@ def run_xt(args):
     def step(plain=False):
         ctx.extend(*d, wl.scoring, plain=plain, out=out, cells=cells, stream=stream)
 
+    rates = measure_int_rates(local)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     cells_step = int(cells.sum().item())
-    ops_step, packed_frac = algorithmic_ops(b, cells.cpu().numpy(), wl.scoring)
+    updates_step, packed_frac = cell_updates(b, cells.cpu().numpy(), wl.scoring)
     sampler = ClockSampler(local)
     barrier(world)
     torch.cuda.synchronize()
@@ -406,8 +473,8 @@ def run_xt(args):
     total_pairs = n * world
     value = cells_per_s / 1e9
     dp_ms = st["dp_ms"] / max(1, st["timed_calls"])
-    peak = SMS * LANES * MAX_MHZ * 1e6 / 1e12
-    achieved = ops_step / (dp_ms / 1e3) / 1e12
+    run_mhz = clocks["sm_mhz"] if clocks else MAX_MHZ
+    roof = int_roofline(updates_step, dp_ms, rates, run_mhz)
     traffic = profiled_traffic(wl.name)
     res = {
         "metric": METRIC, "value": round(value, 3), "unit": "GCUPS", "n_gpus": world,
@@ -424,15 +491,17 @@ def run_xt(args):
                    "parallelism": f"dp{world} (pairs sharded, no collective)"},
         "ext_per_s": round(total_pairs / (ms_max / 1e3), 1),
         "gpu_launches": launches,
-        "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
-                     "unit": "Tops/s (int-ALU instructions)",
-                     "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "kernel": "extension DP launches of one step (k_lane packed/32-bit, k_queue)",
-                     "kernel_ms_per_step": round(dp_ms, 4),
-                     "ops_per_cell": {"packed16x2": OPS_PER_CELL_PACKED,
-                                      "int32": OPS_PER_CELL_INT32},
-                     "packed_cell_fraction": round(packed_frac, 4),
-                     "peak_basis": "issue peak, derived: 152 SMs x 128 lanes x 2070 MHz (max clock)"},
+        "roofline": dict(roof, **{
+            "traffic": traffic,
+            "kernel": "extension DP launches of one step (k_lane packed/32-bit, k_queue)",
+            "kernel_ms_per_step": round(dp_ms, 4),
+            "cell_updates_per_step": updates_step,
+            "ops_per_update": {"alu_pipe": ALU_OPS_PER_UPDATE, "mad_pipe": MAD_OPS_PER_UPDATE,
+                               "note": "one update = one 32-bit cell or two packed 16-bit cells"},
+            "packed_cell_fraction": round(packed_frac, 4),
+            "cell_update_ceiling_gcups": round(rates["cell_update_cells"] * rates["sms"]
+                                               * run_mhz * 1e6 / 1e9, 1),
+            "measured_rates": rates}),
         "clocks": clocks,
         "tuning": tuning or "built-in schedule",
     }
@@ -453,11 +522,13 @@ def run_xt(args):
     if not args.no_ascii:
         res["ascii_reads"] = ascii_leg(b, wl, args, local, stream, cells_step)
     if not args.no_bwa:
-        res["bwa_compatible"] = bwa_leg(b, wl, args, local, stream)
+        res["bwa_compatible"] = bwa_leg(b, wl, args, local, stream, rates, run_mhz)
     if not args.no_e2e:
         res["e2e"] = e2e_leg(ctx, b, wl, args, dev, stream, world)
     if not args.no_x2 and world == 1:
         res["paper_x2"] = x2_leg(local, stream)
+    if not args.no_c4 and world == 1 and args.workload != "c4_long":
+        res["c4_long"] = c4_leg(args, local, stream, rates, run_mhz)
     if not args.no_serve and world == 1:
         res["serving"] = serve_leg(args, local, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -503,7 +574,7 @@ def ascii_leg(b, wl, args, local, stream, cells_step):
                      "pass per call, then the same extension"}
 
 
-def bwa_leg(b, wl, args, local, stream):
+def bwa_leg(b, wl, args, local, stream, rates, mhz):
     """The same batch under the BWA-MEM-compatible semantics
     (xt_extend_batch_bwa: gaps from the match value, band narrowing from the
     end bonus 5, row trimming; the workload's penalties for both gap kinds).
@@ -531,16 +602,70 @@ def bwa_leg(b, wl, args, local, stream):
     ms = e0.elapsed_time(e1) / reps
     n_cells = int(cells.sum().item())
     ctx.close()
-    achieved = n_cells * BWA_OPS_PER_CELL / (ms / 1e3) / 1e12
-    peak = SMS * LANES * MAX_MHZ * 1e6 / 1e12
     return {"value": round(n_cells / (ms / 1e3) / 1e9, 3), "unit": "GCUPS",
             "ms_per_step": round(ms, 4), "useful_cells": n_cells,
             "ext_per_s": round(b.n / (ms / 1e3), 1),
-            "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
-                         "unit": "Tops/s (int-ALU instructions)", "frac": round(achieved / peak, 4),
-                         "ops_per_cell": BWA_OPS_PER_CELL},
+            "roofline": dict(int_roofline(n_cells, ms, rates, mhz, BWA_ALU_OPS_PER_CELL,
+                                          BWA_OPS_PER_CELL),
+                             ops_per_cell={"alu_pipe": BWA_ALU_OPS_PER_CELL,
+                                           "all": BWA_OPS_PER_CELL},
+                             kernel="whole call (classify, order, k_bwa)"),
             "scoring": list(sc.as_tuple()),
             "kernel": "k_bwa: one pair per group of 2..256 lanes, a row's live columns at a time, int32"}
+
+
+def c4_leg(args, local, stream, rates, mhz):
+    """c4_long at its stated size: 250,000 pairs, query lengths log-uniform in
+    [1000, 10000], w = 500, z-drop 400, 32-bit scores (the score bound rules
+    out the packed form), the whole batch in one call with the built-in
+    count-aware plan; the plain kernel on the same batch beside it."""
+    import torch
+    import paper_2301_09310_gb300 as xt
+    from paper_2301_09310_gb300 import synth
+
+    wl = synth.WORKLOADS["c4_long"]
+    b = synth.generate(wl)
+    dev = torch.device("cuda", local)
+    d = [torch.from_numpy(a).to(dev) for a in
+         (b.q_seq, b.q_off, b.q_len, b.t_seq, b.t_off, b.t_len, b.h0)]
+    out = torch.empty((b.n, 7), dtype=torch.int32, device=dev)
+    cells = torch.empty(b.n, dtype=torch.int64, device=dev)
+    ctx = xt.Context(local)
+    for _ in range(2):
+        ctx.extend(*d, wl.scoring, out=out, cells=cells, stream=stream)
+    torch.cuda.synchronize()
+    n_cells = int(cells.sum().item())
+    updates, packed_frac = cell_updates(b, cells.cpu().numpy(), wl.scoring)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.extend(*d, wl.scoring, out=out, cells=cells, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    ctx.set_timing(True)
+    ctx.stats()
+    ctx.extend(*d, wl.scoring, out=out, cells=cells, stream=stream)
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    ctx.set_timing(False)
+    dp_ms = st["dp_ms"] / max(1, st["timed_calls"])
+    e0.record(stream)
+    ctx.extend(*d, wl.scoring, plain=True, out=out, cells=cells, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    pms = e0.elapsed_time(e1)
+    ctx.close()
+    return {"value": round(n_cells / (ms / 1e3) / 1e9, 3), "unit": "GCUPS",
+            "ms_per_step": round(ms, 3), "ext_per_s": round(b.n / (ms / 1e3), 1),
+            "useful_cells": n_cells, "pairs": b.n, "scoring": wl.scoring.as_tuple(),
+            "dtype": "int32" if packed_frac <= 0.0 else "int16x2+int32",
+            "workload": f"c4_long: {WORKLOAD_TEXT['c4_long']}",
+            "plain": {"value": round(n_cells / (pms / 1e3) / 1e9, 3), "unit": "GCUPS",
+                      "ms_per_step": round(pms, 3)},
+            "roofline": dict(int_roofline(updates, dp_ms, rates, mhz),
+                             kernel_ms_per_step=round(dp_ms, 3))}
 
 
 def e2e_leg(ctx, b, wl, args, dev, stream, world):

@@ -84,3 +84,26 @@ def test_bwa_full_batch_sampled_against_oracle(ctx):
     bad = np.nonzero(np.any(out[idx] != want_out, axis=1) | (cells[idx] != want_cells))[0]
     assert bad.size == 0, (f"{bad.size} of 6000 sampled pairs differ; first pair #{idx[bad[0]]}: "
                            f"gpu {out[idx][bad[0]].tolist()} oracle {want_out[bad[0]].tolist()}")
+
+
+def test_c4_full_batch_sampled_against_oracle(ctx):
+    """All 250,000 long pairs of c4_long (w = 500, z-drop 400) in one call, as
+    bench.py's c4 leg times it.  Together the long buckets hold more than two
+    full waves of one-lane slots, so the count-aware plan takes one lane per
+    pair with 16-row strips for every bucket of queries over 510 bases; 2,000
+    sampled pairs are compared with the oracle on every field and on cells,
+    and every pair is checked for the properties above."""
+    wl = synth.WORKLOADS["c4_long"]
+    b = synth.generate(wl)
+    assert b.n == 250_000
+    out, cells = run_gpu(ctx, b, wl.scoring)
+    check_properties(b, out, cells, wl.scoring)
+    rng = np.random.default_rng(2304)
+    idx = np.sort(rng.choice(b.n, size=2000, replace=False))
+    sub = b.take(idx)
+    want_out, want_cells = run_oracle(sub, wl.scoring)
+    got_out, got_cells = out[idx], cells[idx]
+    bad = np.nonzero(np.any(got_out != want_out, axis=1) | (got_cells != want_cells))[0]
+    assert bad.size == 0, (f"{bad.size} of 2000 sampled pairs differ; first pair "
+                           f"#{idx[bad[0]]}: gpu {got_out[bad[0]].tolist()} cells {got_cells[bad[0]]}"
+                           f" oracle {want_out[bad[0]].tolist()} cells {want_cells[bad[0]]}")

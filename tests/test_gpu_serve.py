@@ -198,3 +198,50 @@ def test_server_with_tuning_table(xt, tmp_path):
     with pytest.raises(xt.XtError) as e:
         xt.Server(0, slots=1, tuning_path=str(tmp_path / "missing.json"))
     assert e.value.status == xt.XT_EINVAL
+
+
+def test_full_stream_10m_equals_batched(xt):
+    """The served stream at its stated size: 10,000,000 c5 pairs cut into
+    requests of U[1, 4096] pairs, all submitted as fast as the queue admits
+    them (as the 90% load level does when it falls behind).  Every request's
+    results equal one batched call on the whole stream; a sample of pairs is
+    also compared with the oracle."""
+    import torch
+    from tests.gpu_util import to_dev
+    b = synth.generate(WL, n=10_000_000)
+    rs = synth.request_stream(b, 1e9, seed=5)
+    ctx = xt.Context(0)
+    try:
+        o, c = ctx.extend(*to_dev(b, torch.device("cuda", 0)), WL.scoring)
+        torch.cuda.synchronize()
+        ref_out, ref_cells = o.cpu().numpy(), c.cpu().numpy()
+        del o, c
+    finally:
+        ctx.close()
+    torch.cuda.empty_cache()
+    nreq = int(rs.size.size)
+    got = [None] * nreq
+    srv = xt.Server(0, slots=3, mem_budget_bytes=40 * 10**9)
+    try:
+        tickets = []
+
+        def waiter():
+            for k in range(nreq):
+                while k >= len(tickets):
+                    threading.Event().wait(1e-4)
+                got[k] = srv.wait(tickets[k], timeout_s=300)[:2]
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        for k in range(nreq):
+            tickets.append(srv.submit(*rs.request(k), WL.scoring, retry_busy=True))
+        th.join()
+    finally:
+        srv.close()
+    for k in range(nreq):
+        a, n = int(rs.start[k]), int(rs.size[k])
+        check(got[k][0], got[k][1], (ref_out[a:a + n], ref_cells[a:a + n]), f"request {k}")
+    rng = np.random.default_rng(2305)
+    idx = np.sort(rng.choice(b.n, size=3000, replace=False))
+    want_out, want_cells = run_oracle(b.take(idx), WL.scoring)
+    check(ref_out[idx], ref_cells[idx], (want_out, want_cells), "sampled pairs vs oracle")
