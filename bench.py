@@ -180,11 +180,28 @@ def reduce(world, value, op):
     return float(t.item())
 
 
-def shard_of(rank: int, n_per_gpu: int) -> tuple[int, int]:
-    """Weak scaling: rank r extends pairs [r * n, (r + 1) * n) of the
-    workload's counter-based stream, so shards are disjoint and every rank's
-    pairs are the same whatever the number of ranks."""
-    return rank * n_per_gpu, n_per_gpu
+def shard_of(rank: int, world: int, n_per_gpu: int, wl):
+    """Weak scaling: the job is the first world * n_per_gpu pairs of the
+    workload's counter-based stream, split over the ranks by the library's
+    LPT partitioner on estimated cells (xt_shard_lpt; every rank computes the
+    same split from the pairs' lengths alone).  Returns this rank's stream
+    indices (all of [0, n) on one GPU) and the estimated cells of every part."""
+    import paper_2301_09310_gb300 as xt
+    from paper_2301_09310_gb300 import synth
+    n_job = world * n_per_gpu
+    if world == 1:
+        return np.arange(n_per_gpu, dtype=np.int64), None
+    q_len, t_len, _ = synth.shapes(wl, n=n_job)
+    shard, part_cells = xt.xt_shard_lpt(q_len, t_len, wl.scoring.w, world)
+    return np.nonzero(shard == rank)[0].astype(np.int64), part_cells
+
+
+def batch_of(wl, idx, n_per_gpu):
+    """This rank's pairs: the contiguous prefix on one GPU, else by index."""
+    from paper_2301_09310_gb300 import synth
+    if idx.size == n_per_gpu and (idx.size == 0 or int(idx[-1]) == idx.size - 1):
+        return synth.generate(wl, n=n_per_gpu)
+    return synth.generate_at(wl, idx)
 
 
 def aggregate(world, units_local: float, seconds_local: float):
@@ -385,9 +402,10 @@ def run_xt(args):
     from paper_2301_09310_gb300 import build as xbuild
     xbuild.build()
     wl = synth.WORKLOADS[args.workload]
-    n = args.pairs or wl.n_pairs
-    first, n = shard_of(rank, n)
-    b = synth.generate(wl, n=n, first=first)
+    n_per_gpu = args.pairs or wl.n_pairs
+    idx, part_cells = shard_of(rank, world, n_per_gpu, wl)
+    b = batch_of(wl, idx, n_per_gpu)
+    n = b.n
     dev = torch.device("cuda", local)
     T = lambda a: torch.from_numpy(a).to(dev)  # noqa: E731
     d = [T(b.q_seq), T(b.q_off), T(b.q_len), T(b.t_seq), T(b.t_off), T(b.t_len), T(b.h0)]
@@ -470,7 +488,7 @@ def run_xt(args):
     ctx.set_timing(False)
     total_cells, s_max, cells_per_s = aggregate(world, cells_step, ms / 1e3)
     ms_max = s_max * 1e3
-    total_pairs = n * world
+    total_pairs = reduce(world, n, _sum_op() if world > 1 else None)
     value = cells_per_s / 1e9
     dp_ms = st["dp_ms"] / max(1, st["timed_calls"])
     run_mhz = clocks["sm_mhz"] if clocks else MAX_MHZ
@@ -488,7 +506,9 @@ def run_xt(args):
                    "pairs_per_gpu": n, "scoring": wl.scoring.as_tuple(),
                    "useful_cells_per_gpu": cells_step,
                    "l2": f"inputs {b.nbytes() / 1e9:.2f} GB per GPU > 129 MB L2, no flush",
-                   "parallelism": f"dp{world} (pairs sharded, no collective)"},
+                   "parallelism": (f"dp{world}: the first {world} x {n_per_gpu} pairs split by "
+                                   "LPT on estimated cells (xt_shard_lpt), no collective"
+                                   if world > 1 else "dp1")},
         "ext_per_s": round(total_pairs / (ms_max / 1e3), 1),
         "gpu_launches": launches,
         "roofline": dict(roof, **{

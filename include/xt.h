@@ -385,6 +385,26 @@ xt_status xt_extend_batch_bwa(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_bytes
                               xt_result* out, int64_t* cells_out, void* stream);
 
 /*
+ * Split a batch over `parts` devices (host call, no GPU needed).  Pairs are
+ * independent (Sec. VII-C: several GPUs partition the pairs and exchange
+ * nothing but results), so each device extends its own part with
+ * xt_extend_batch and the results are put back in input order by the
+ * caller.  The split is LPT on estimated cells: each pair's estimate is its
+ * in-band cells with no z-drop under band w (rows i < min(tlen, qlen + w));
+ * pairs go in decreasing order of the estimate (ties: lower pair index
+ * first) to the part with the smallest estimated total so far (ties: lower
+ * part index), which keeps the largest part within 4/3 of the best possible
+ * split and, for batches of many small pairs, within one pair of the mean.
+ * Deterministic: every rank that calls it on the same lengths gets the same
+ * split.  Host arrays: q_len, t_len int32[n_pairs] (negative lengths count
+ * as 0); shard int32[n_pairs] receives each pair's part in [0, parts);
+ * part_cells int64[parts] (may be NULL) each part's estimated cells.
+ * XT_EINVAL for n_pairs < 0, w < 0, parts outside [1, 4096] or a NULL array.
+ */
+xt_status xt_shard_lpt(const int32_t* q_len, const int32_t* t_len, int32_t n_pairs, int32_t w,
+                       int32_t parts, int32_t* shard, int64_t* part_cells);
+
+/*
  * Measurement aid (not part of the method): the throughput of one kind of
  * integer instruction on `device`, which sets the roofline of the extension
  * DP (integer arithmetic, no dense contraction).  A probe kernel runs the

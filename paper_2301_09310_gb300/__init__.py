@@ -31,7 +31,7 @@ EXPORTED = ("xt_ctx_create", "xt_ctx_destroy", "xt_ctx_sync", "xt_extend_batch",
             "xt_ctx_load_tuning", "xt_ctx_set_bucket_schedule_for",
             "xt_ctx_get_bucket_schedule_for", "xt_extend_batch_begin", "xt_extend_batch_ready",
             "xt_extend_batch_finish", "xt_ctx_set_alphabet", "xt_extend_seeds",
-            "xt_extend_batch_bwa", "xt_bwa_scoring_check", "xt_int_rate")
+            "xt_extend_batch_bwa", "xt_bwa_scoring_check", "xt_int_rate", "xt_shard_lpt")
 XT_STATIC_MAX_PAIRS = 1 << 20
 # instruction kinds of xt_int_rate (measurement aid)
 XT_RATE_ADD16X2, XT_RATE_MAX3_16X2, XT_RATE_ADDMAX_16X2, XT_RATE_PRMT = 0, 1, 2, 3
@@ -174,6 +174,8 @@ def load_library(path: str | None = None):
     lib.xt_int_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                 ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
     lib.xt_int_rate.restype = ctypes.c_int
+    lib.xt_shard_lpt.argtypes = [P, P, I32, I32, I32, P, P]
+    lib.xt_shard_lpt.restype = ctypes.c_int
     lib.xt_now_ns.argtypes = []
     lib.xt_now_ns.restype = ctypes.c_int64
     lib.xt_serve_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(xt_serve_config)]
@@ -270,6 +272,23 @@ def xt_ctx_set_alphabet(ctx: int, alphabet: int) -> int:
 
 def xt_ctx_set_streams(ctx: int, branches: int) -> int:
     return load_library().xt_ctx_set_streams(ctypes.c_void_p(ctx), int(branches))
+
+
+def xt_shard_lpt(q_len, t_len, w: int, parts: int):
+    """(shard int32[n], part_cells int64[parts]): the LPT split of a batch
+    over `parts` devices by estimated cells (host arrays in, host arrays out)."""
+    import numpy as np
+    ql = np.ascontiguousarray(q_len, np.int32)
+    tl = np.ascontiguousarray(t_len, np.int32)
+    if ql.shape != tl.shape:
+        raise ValueError("q_len and t_len differ in length")
+    shard = np.empty(ql.size, np.int32)
+    cells = np.empty(max(int(parts), 1), np.int64)
+    s = load_library().xt_shard_lpt(ql.ctypes.data, tl.ctypes.data, int(ql.size), int(w),
+                                    int(parts), shard.ctypes.data, cells.ctypes.data)
+    if s != XT_OK:
+        raise XtError(s, "xt_shard_lpt")
+    return shard, cells
 
 
 def xt_int_rate(device: int, op: int, reps: int = 3):

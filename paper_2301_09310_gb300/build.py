@@ -21,7 +21,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 CU_SOURCES = ["xt_api.cu", "xt_kernels.cu", "xt_serve.cpp", "xt_tune.cu", "xt_bwa.cu", "xt_stage.cu",
-              "xt_peak.cu"]
+              "xt_peak.cu", "xt_shard.cu"]
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

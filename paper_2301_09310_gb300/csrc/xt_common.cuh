@@ -85,7 +85,7 @@ __device__ __forceinline__ int32_t row_m1(int32_t c, int32_t h0, const Score& sc
 
 // Sum of in-band widths of rows 0..n (n < qlen + w, so every width is > 0):
 //   sum_i min(qlen, i + w + 1) - sum_i max(0, i - w).
-__device__ __forceinline__ int64_t band_cells_upto(int64_t n, int64_t qlen, int64_t w) {
+__host__ __device__ __forceinline__ int64_t band_cells_upto(int64_t n, int64_t qlen, int64_t w) {
   if (n < 0) return 0;
   int64_t a;
   const int64_t k = qlen - w - 1;  // rows i <= k have i + w + 1 <= qlen

@@ -1,7 +1,9 @@
 // xt_kernels.cu -- classify/bucket, ordering, persistent queue kernels and the
 // plain one-pair-per-block kernel.
 #include <cstdio>
+#include <map>
 #include <mutex>
+#include <utility>
 
 #include "xt_engine.cuh"
 #include "xt_kernels.cuh"
@@ -513,21 +515,21 @@ constexpr size_t kStaticSmemMax = 1024;
 // host threads at once.  The limit is therefore only ever raised, under a
 // lock, never set back to a smaller launch's size: it is a cap, and each
 // launch's occupancy still follows its own dynamic size.
-constexpr int kAttrDevices = 64;
+std::mutex g_smem_mu;
+std::map<std::pair<const void*, int>, int> g_smem_limit;  // (kernel, device) -> limit set
 
 template <typename K>
 cudaError_t raise_smem_limit(K kern, size_t smem) {
-  static std::mutex mu;
-  static int limit[kAttrDevices] = {};
   if (smem + kStaticSmemMax <= 48 * 1024) return cudaSuccess;  // the default limit covers it
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  std::lock_guard<std::mutex> lk(mu);
-  const bool tracked = dev >= 0 && dev < kAttrDevices;
-  if (tracked && limit[dev] >= (int)smem) return cudaSuccess;
+  const std::pair<const void*, int> key(reinterpret_cast<const void*>(kern), dev);
+  std::lock_guard<std::mutex> lk(g_smem_mu);
+  auto it = g_smem_limit.find(key);
+  if (it != g_smem_limit.end() && it->second >= (int)smem) return cudaSuccess;
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess && tracked) limit[dev] = (int)smem;
+  if (e == cudaSuccess) g_smem_limit[key] = (int)smem;
   return e;
 }
 

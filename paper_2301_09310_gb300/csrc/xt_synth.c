@@ -195,3 +195,47 @@ void xs_fill(const xs_config* c, uint64_t first, int64_t n, const int64_t* q_off
   fill_worker(&f);
   for (int k = 0; k < started; ++k) pthread_join(th[k], NULL);
 }
+
+/* Lengths and h0 of the pairs idx[0..n) of the workload's stream (pair k's
+ * shape depends on k alone, so any subset can be drawn). */
+void xs_shapes_at(const xs_config* c, const int64_t* idx, int64_t n, int32_t* q_len,
+                  int32_t* t_len, int32_t* h0) {
+  for (int64_t i = 0; i < n; ++i) {
+    pair_shape s = shape_of(c, (uint64_t)idx[i]);
+    q_len[i] = s.qlen;
+    t_len[i] = s.tlen;
+    h0[i] = s.h0;
+  }
+}
+
+typedef struct {
+  const xs_config* c; const int64_t* idx; int64_t n;
+  const int64_t* q_off; const int64_t* t_off; uint8_t* q_seq; uint8_t* t_seq;
+  int64_t next;
+} fill_at_job;
+
+static void* fill_at_worker(void* arg) {
+  fill_at_job* f = (fill_at_job*)arg;
+  for (;;) {
+    int64_t s = __atomic_fetch_add(&f->next, 256, __ATOMIC_RELAXED);
+    if (s >= f->n) break;
+    int64_t e = s + 256 < f->n ? s + 256 : f->n;
+    for (int64_t i = s; i < e; ++i)
+      fill_pair(f->c, (uint64_t)f->idx[i], f->q_seq + f->q_off[i], f->t_seq + f->t_off[i]);
+  }
+  return NULL;
+}
+
+/* Sequences of the pairs idx[0..n) at the given offsets (from xs_shapes_at). */
+void xs_fill_at(const xs_config* c, const int64_t* idx, int64_t n, const int64_t* q_off,
+                const int64_t* t_off, uint8_t* q_seq, uint8_t* t_seq, int nthreads) {
+  fill_at_job f = {c, idx, n, q_off, t_off, q_seq, t_seq, 0};
+  if (nthreads < 1) nthreads = 1;
+  pthread_t th[256];
+  if (nthreads > 256) nthreads = 256;
+  int started = 0;
+  for (int k = 1; k < nthreads; ++k)
+    if (pthread_create(&th[started], NULL, fill_at_worker, &f) == 0) ++started;
+  fill_at_worker(&f);
+  for (int k = 0; k < started; ++k) pthread_join(th[k], NULL);
+}

@@ -193,6 +193,11 @@ def _lib():
         lib.xs_fill.restype = None
         lib.xs_fill.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_uint64, ctypes.c_int64, P, P, P, P,
                                 ctypes.c_int]
+        lib.xs_shapes_at.restype = None
+        lib.xs_shapes_at.argtypes = [ctypes.POINTER(_Cfg), P, ctypes.c_int64, P, P, P]
+        lib.xs_fill_at.restype = None
+        lib.xs_fill_at.argtypes = [ctypes.POINTER(_Cfg), P, ctypes.c_int64, P, P, P, P,
+                                   ctypes.c_int]
         _LIB = lib
     return _LIB
 
@@ -259,6 +264,40 @@ def generate(wl: Workload, n: int | None = None, first: int = 0,
         nthreads = os.cpu_count() or 1
     lib.xs_fill(ctypes.byref(cfg), first, n, _p(q_off), _p(t_off), _p(q_seq), _p(t_seq),
                 int(nthreads))
+    return Batch(q_seq, q_off, q_len, t_seq, t_off, t_len, h0)
+
+
+def shapes(wl: Workload, n: int | None = None, first: int = 0):
+    """(q_len, t_len, h0) of pairs [first, first+n) without their sequences."""
+    n = wl.n_pairs if n is None else int(n)
+    cfg = wl._c()
+    q_len = np.empty(n, np.int32)
+    t_len = np.empty(n, np.int32)
+    h0 = np.empty(n, np.int32)
+    _lib().xs_shapes(ctypes.byref(cfg), first, n, _p(q_len), _p(t_len), _p(h0))
+    return q_len, t_len, h0
+
+
+def generate_at(wl: Workload, idx, nthreads: int | None = None) -> Batch:
+    """The pairs of workload wl with the given stream indices, in that order
+    (pair k is the same pair generate() gives at position k)."""
+    idx = np.ascontiguousarray(idx, np.int64)
+    n = int(idx.size)
+    cfg = wl._c()
+    lib = _lib()
+    q_len = np.empty(n, np.int32)
+    t_len = np.empty(n, np.int32)
+    h0 = np.empty(n, np.int32)
+    lib.xs_shapes_at(ctypes.byref(cfg), _p(idx), n, _p(q_len), _p(t_len), _p(h0))
+    q_off = np.zeros(n, np.int64)
+    t_off = np.zeros(n, np.int64)
+    if n > 1:
+        np.cumsum(q_len[:-1], dtype=np.int64, out=q_off[1:])
+        np.cumsum(t_len[:-1], dtype=np.int64, out=t_off[1:])
+    q_seq = np.empty(int(q_len.sum(dtype=np.int64)), np.uint8)
+    t_seq = np.empty(int(t_len.sum(dtype=np.int64)), np.uint8)
+    lib.xs_fill_at(ctypes.byref(cfg), _p(idx), n, _p(q_off), _p(t_off), _p(q_seq), _p(t_seq),
+                   int(nthreads or os.cpu_count() or 1))
     return Batch(q_seq, q_off, q_len, t_seq, t_off, t_len, h0)
 
 
