@@ -348,10 +348,11 @@ xt_status xt_scoring_check(const xt_scoring* sc);
  *   band narrowing: with gain = qlen*match + end_bonus, w_x = 1 if gain < o_x,
  *     else (gain - o_x) / e_x + 1 (x = ins, del), and the band is |i - j| <=
  *     min(w, w_ins, w_del) =: w';
- *   row trimming: row 0 computes [0, min(qlen, w'+1)); if [a, b] is the
- *     maximal run of computed columns of row i with H > 0 that holds the row's
- *     best column mj (the largest column of the row maximum m), row i+1
- *     computes [max(a, i+1-w'), min(b+2, i+w'+2, qlen));
+ *   row trimming: row 0 computes [0, min(qlen, w'+1)); the dead cells at
+ *     both ends of a row are dropped: if a and b are the first and the last
+ *     computed column of row i with H > 0, row i+1 computes
+ *     [max(a, i+1-w'), min(b+2, i+w'+2, qlen)) (dead columns between a and b
+ *     are computed again);
  *   after each row, in order: if the row computed column qlen-1 and H(i,
  *     qlen-1) >= gscore, gscore = that value and gtle = i+1 (the latest row
  *     wins ties; gscore starts at -1); the extension stops if m = 0; a new

@@ -236,11 +236,14 @@ void xo_extend_one(const uint8_t* q, int32_t qlen, const uint8_t* t, int32_t tle
  *        w'  = min(w, w_ins, w_del)
  *      and the band is |i - j| <= w'.
  *   V5 row trimming: row 0 computes columns [0, min(qlen, w'+1)).  After row
- *      i, let [a, b] be the maximal run of consecutive computed columns with
- *      H > 0 that holds mj_i; row i+1 computes
+ *      i, the dead cells at the two ends of its computed range are dropped:
+ *      with a the first and b the last computed column of row i with H > 0,
+ *      row i+1 computes
  *        [max(a, i+1-w'), min(b+2, i+w'+2, qlen))
- *      i.e. only the columns that run reaches in one step (a vertical step
- *      from a, a diagonal step from b).
+ *      i.e. the columns its live cells reach in one step (a vertical step
+ *      from a, a diagonal step from b); dead columns between a and b are
+ *      computed again.  (A cell with H = 0 also has M <= 0 and F = 0, so the
+ *      next row's deletion state there is 0: H alone decides.)
  *   V6 rows: m_i and mj_i are taken over the computed columns (largest j on
  *      ties).  After row i, in this order:
  *        gscore: if row i computed column qlen-1 and H(i,qlen-1) >= gscore,
@@ -382,10 +385,11 @@ void xo_extend_one_bwa(const uint8_t* q, int32_t qlen, const uint8_t* t, int32_t
       const int64_t drop = di > dj ? best - m - (di - dj) * e_del : best - m - (dj - di) * e_ins;
       if (drop > sc->zdrop) break;
     }
-    /* V5: the run of live cells around mj. */
-    int64_t a = mj, b = mj;
-    while (a - 1 >= beg && Hc[a] > 0) --a;     /* Hc[a] holds column a-1 */
-    while (b + 1 < end && Hc[b + 2] > 0) ++b;  /* Hc[b+2] holds column b+1 */
+    /* V5: the first and the last live column of the row (m > 0 here, so both
+     * exist inside [beg, end)). */
+    int64_t a = beg, b = end - 1;
+    while (Hc[a + 1] == 0) ++a;  /* Hc[a+1] holds column a */
+    while (Hc[b + 1] == 0) --b;
     if (flags & XO_BWA_NO_TRIM) { next_beg = 0; next_end = qlen; }
     else { next_beg = a; next_end = b + 2; }
     int64_t* tmp;

@@ -1,15 +1,15 @@
 // xt_bwa.cu -- the BWA-MEM-compatible extension (xt_extend_batch_bwa).
 //
 // The variant (stated in full in include/xt.h) opens gaps from the match value
-// M rather than from H and trims each row to the live run around the row's
-// best cell.  Both change how the work parallelises:
+// M rather than from H and drops the dead cells at both ends of each row.
+// Both change how the work parallelises:
 //
 //  * the insertion chain E of a row depends only on that row's M values,
 //    E(i,j) = max(0, max_{k<j} (M(i,k) - o_ins - e_ins*(j-k))), a max-plus
 //    prefix scan over the row, and M and F depend only on the row above: a row
 //    is data-parallel across its columns;
-//  * trimming makes row i+1's columns depend on all of row i (the run around
-//    the row maximum), so rows must go one after another -- the strip scheme
+//  * trimming makes row i+1's columns depend on all of row i (its first and
+//    last live cells), so rows must go one after another -- the strip scheme
 //    of the default kernels, which keeps several rows in flight, does not
 //    apply.
 //
@@ -20,7 +20,7 @@
 // columns each, and the row above lives in shared memory rather than in fixed
 // registers.  Per row the group runs an exclusive max-scan for the insertion
 // chain, a max-reduction for the row maximum and its column, and a min/max
-// reduction for the live run.  G*K is the smallest power of two >= min(qlen,
+// reduction for the row's first and last live columns.  G*K is the smallest power of two >= min(qlen,
 // 2w'+1), from 64 to 8192 columns; up to 32 lanes a group is a warp segment
 // (shuffles), above that a whole CTA (shuffles plus shared memory).  Pairs are
 // classified by G*K, and each class runs a persistent kernel whose groups take
@@ -508,18 +508,15 @@ __device__ __forceinline__ void bwa_pair(const BwaArgs& a, const Group<G>& g, in
                                    : (int64_t)best - m - (dj - di) * e_ins;
       if (drop > sc.zdrop) break;
     }
-    // the live run around the best column: the last dead column below it and
-    // the first dead column above it (columns outside [beg, end) are dead)
-    const int32_t rel = mj - first;
-    const uint32_t below = rel <= 0 ? 0u : (rel >= cnt ? dead : dead & ((1u << rel) - 1u));
-    const uint32_t above =
-        rel >= cnt - 1 ? 0u : (rel < 0 ? dead : dead & ~((2u << rel) - 1u));
-    int32_t zb = below ? first + 31 - __clz(below) : beg - 1;
-    int32_t za = above ? first + __ffs(above) - 1 : end;
-    g.all_max_min(&zb, &za);
-    // next row: the run's columns reachable in one step, within the band
-    beg = max(zb + 1, i + 1 - w);
-    end = min(min(za + 1, i + w + 2), qlen);
+    // the first and the last live column of the row (the row maximum is > 0,
+    // so some lane holds one); the dead cells at both ends are dropped
+    const uint32_t live = (cnt >= 32 ? 0xffffffffu : (1u << cnt) - 1u) & ~dead;
+    int32_t ll = live ? first + 31 - __clz(live) : -1;
+    int32_t fl = live ? first + __ffs(live) - 1 : INT_MAX;
+    g.all_max_min(&ll, &fl);
+    // next row: the columns the live cells reach in one step, within the band
+    beg = max(fl, i + 1 - w);
+    end = min(min(ll + 2, i + w + 2), qlen);
   }
   if (lane == 0) put_result(a, k, best, bj + 1, bi + 1, gscore, gtle, max_off, XT_OK, cells);
   g.sync();  // the buffer is free for the group's next pair

@@ -138,17 +138,15 @@ def extend_by_rows(q, t, h0, sc, G, odd, early_f=False):
             drop = best - m - ((di - dj) * sc.e_del if di > dj else (dj - di) * sc.e_ins)
             if drop > sc.zdrop:
                 break
-        zb, za = beg - 1, end
+        ll, fl = -1, None
         for (first, cnt, _, _, _), dm in zip(lanes, dead):
             for kk in range(cnt):
-                if dm >> kk & 1:
+                if not dm >> kk & 1:
                     j = first + kk
-                    if j < mj:
-                        zb = max(zb, j)
-                    elif j > mj:
-                        za = min(za, j)
-        beg = max(zb + 1, i + 1 - w)
-        end = min(za + 1, i + w + 2, qlen)
+                    ll = max(ll, j)
+                    fl = j if fl is None else min(fl, j)
+        beg = max(fl, i + 1 - w)
+        end = min(ll + 2, i + w + 2, qlen)
     return (best, bj + 1, bi + 1, gscore, gtle, max_off, 0), cells
 
 

@@ -52,6 +52,24 @@ def test_handworked_trimming_table():
     assert list(tu.result) == u["result"] and tu.cells == u["cells"]
 
 
+def test_handworked_trimming_keeps_interior_dead_cells():
+    """Row trimming drops only the dead cells at the two ends of a row: a row
+    with two live cells and a dead one between them computes all three next
+    row, and the far cell's descendants reach the last query column."""
+    g = load("handworked_bwa_trim_ends_3x3.json")
+    sc = BwaScoring(**g["scoring"])
+    tr = oracle.extend_one_bwa(g["q"], g["t"], g["h0"], sc, trace=True)
+    for k in ("H", "M", "E", "F"):
+        assert getattr(tr, k).tolist() == g[k], k
+    assert tr.row_beg.tolist() == g["row_beg"]
+    assert tr.row_end.tolist() == g["row_end"]
+    assert tr.row_m.tolist() == g["row_m"]
+    assert tr.row_mj.tolist() == g["row_mj"]
+    assert list(tr.result) == g["result"] and tr.cells == g["cells"]
+    # the earlier live-run reading gives a different gscore on this pair
+    assert g["live_run_rule"]["result"] != g["result"]
+
+
 def test_handworked_zdrop_insertion_direction():
     g = load("handworked_bwa_zdrop_ins_3x4.json")
     for case in g["cases"]:

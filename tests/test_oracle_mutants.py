@@ -109,6 +109,8 @@ BWA_MUTANTS = {
     "bwa_gscore_earliest_row": ("Hc[qlen] >= gscore", "Hc[qlen] > gscore"),
     "bwa_gscore_positive_only": ("end == qlen && Hc[qlen] >= gscore",
                                  "end == qlen && Hc[qlen] > 0 && Hc[qlen] >= gscore"),
+    "bwa_trim_live_run_only": ("    int64_t a = beg, b = end - 1;\n    while (Hc[a + 1] == 0) ++a;  /* Hc[a+1] holds column a */\n    while (Hc[b + 1] == 0) --b;",
+                               "    int64_t a = mj, b = mj;\n    while (a - 1 >= beg && Hc[a] > 0) --a;\n    while (b + 1 < end && Hc[b + 2] > 0) ++b;"),
     "bwa_trim_drops_run_start": ("else { next_beg = a; next_end = b + 2; }",
                                  "else { next_beg = a + 1; next_end = b + 2; }"),
     "bwa_trim_no_diagonal_step": ("else { next_beg = a; next_end = b + 2; }",
@@ -140,6 +142,7 @@ def build_bwa_mutant(name, tmp):
 def bwa_pins_fail():
     checks = [
         bwa_pins.test_handworked_trimming_table,
+        bwa_pins.test_handworked_trimming_keeps_interior_dead_cells,
         bwa_pins.test_handworked_zdrop_insertion_direction,
         bwa_pins.test_boundary_runs_by_enumeration,
         bwa_pins.test_insertion_then_deletion_is_not_a_path,
