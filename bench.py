@@ -249,7 +249,7 @@ def measure_int_rates(local):
             "ms": {k: round(ms, 4) for k, (_, ms) in raw.items()},
             "sm_mhz": mhz, "sms": sms, "clocks": clocks,
             "alu_pipe": max(per_clk[k] for k in ALU_PROBES),
-            "mad_pipe": per_clk["imad.u32"], "issue": per_clk["max3.s16x2 + imad.u32 alternating"],
+            "mad_pipe": per_clk["imad.u32"], "issue": per_clk["add.s16x2 + imul.u32 alternating"],
             "cell_update_cells": per_clk["packed cell update (cells)"]}
 
 
@@ -281,7 +281,13 @@ def int_roofline(updates, kernel_ms, rates, mhz, alu_ops=ALU_OPS_PER_UPDATE,
                       "frac": round(all_ach / issue_peak, 4),
                       "basis": f"measured issue probe {rates['issue']:.2f} thread-instr/SM/clk "
                                "(ALU and multiply-add pipes alternating), every algorithmic "
-                               "instruction counted, of measured"}}
+                               "instruction counted, of measured"},
+            "cell_update_ceiling": {
+                "updates_per_s": round(rates["cell_update_cells"] / 2 * clk, 1),
+                "frac": round(updates / sec / (rates["cell_update_cells"] / 2 * clk), 4),
+                "basis": "the packed cell update alone on registers (xt_int_rate "
+                         "XT_RATE_CELL_P16, 16 cells per step, N-base select included): "
+                         "the engine's own arithmetic with no memory, band or row work"}}
 
 
 # the files that define the extension kernels' device code
@@ -913,11 +919,16 @@ def serve_levels(args, local, b, wl, peak_pairs, ref_out, ref_cells, total_cells
                     break
                 if left > 300_000:
                     time.sleep((left - 200_000) / 1e9)
+            backoff = 50e-6
             while True:
                 s = submit(ctypes.c_void_p(srv), *calls[r], ctypes.byref(tk))
                 if s != xt.XT_EBUSY:
                     break
                 busy += 1
+                # the queue drains as batches form: leave the host cores to
+                # the server's gather threads meanwhile
+                time.sleep(backoff)
+                backoff = min(2 * backoff, 1e-3)
             if s != xt.XT_OK:
                 raise RuntimeError(f"xt_serve_submit: {xt.xt_status_str(s)}")
             tickets.put(tk.value)

@@ -412,8 +412,8 @@ xt_status xt_shard_lpt(const int32_t* q_len, const int32_t* t_len, int32_t n_pai
  * instruction in independent chains on every SM (8 chains per thread, a full
  * SM of warps) and is timed with CUDA events after one warm-up launch; the
  * best of `reps` launches is returned: *units instructions (thread-level) in
- * *ms milliseconds.  XT_RATE_MIX alternates a packed 3-way max with a 32-bit
- * multiply-add, two instructions that issue to different pipes, so it
+ * *ms milliseconds.  XT_RATE_MIX alternates a packed add with a 32-bit
+ * multiply, two-source instructions that issue to different pipes, so it
  * measures the issue rate.  XT_RATE_CELL_P16 runs the packed cell update of
  * the one-lane engine on registers (the engine's fast step, 16 cells per step
  * and thread); *units then counts cells.  Synchronous; allocates a few bytes
@@ -426,7 +426,7 @@ xt_status xt_shard_lpt(const int32_t* q_len, const int32_t* t_len, int32_t n_pai
 #define XT_RATE_IADD3 4        /* 32-bit three-input add */
 #define XT_RATE_MAX3_32 5      /* 3-way 32-bit max */
 #define XT_RATE_IMAD 6         /* 32-bit multiply-add */
-#define XT_RATE_MIX 7          /* packed 3-way max and multiply-add, alternating */
+#define XT_RATE_MIX 7          /* packed add and 32-bit multiply, alternating */
 #define XT_RATE_CELL_P16 8     /* the packed cell update (cells, not instructions) */
 xt_status xt_int_rate(int device, int op, int reps, int64_t* units, double* ms);
 

@@ -43,8 +43,14 @@ __device__ __forceinline__ uint32_t op_step(uint32_t a, uint32_t b, uint32_t c, 
     r = (uint32_t)__vimax3_s32((int)a, (int)b, (int)c);
   } else if constexpr (OP == XT_RATE_IMAD) {
     r = a * b + c;
-  } else {  // XT_RATE_MIX: a 3-way packed max and a multiply-add, alternating by chain
-    r = (k & 1) ? a * b + c : __vimax3_s16x2(a, b, c);
+  } else {  // XT_RATE_MIX: a packed add and a multiply, alternating by chain
+    // (two-source instructions of the two integer pipes: three-source ones
+    // alternating are limited by register reads before the issue slots)
+    if (k & 1) {
+      r = a * b;
+    } else {
+      asm("add.s16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    }
   }
   return r;
 }
