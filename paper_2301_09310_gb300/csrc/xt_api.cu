@@ -260,7 +260,8 @@ bool lane_launch(xt_ctx* ctx, const Score& sc, int cls, int j, bool allow_gring,
   if (gring && !allow_gring) return false;
   L->cls = cls; L->j_lo = j; L->j_hi = j; L->lane = true; L->P = 1; L->R = R;
   L->rs_log2 = lg; L->global_ring = gring; L->slab = gring ? ((int64_t)1 << lg) : 0;
-  const size_t smem = (gring ? 0 : ring) + (cls == CLS_PACKED ? lane_stage_bytes(j) : 0);
+  const size_t smem = (gring ? 0 : ring) + (cls == CLS_PACKED ? lane_stage_bytes(j) : 0) +
+                      lane_pipe_bytes(cls, gring);
   const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (size_t)(220 * 1024) / (smem + 1024)));
   L->grid = ctx->num_sms * per_sm;
   int k = 0;

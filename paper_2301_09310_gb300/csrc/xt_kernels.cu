@@ -252,6 +252,9 @@ __global__ void __launch_bounds__(kLaneThreads, 4)
   Query<QSTAGE> qs;
   qs.stage = QSTAGE ? s_dyn + ring_bytes + (size_t)(threadIdx.x >> 5) * (32u << qs_log2) + lane
                     : nullptr;
+  // 32-bit global rings feed their entries through shared-memory slots
+  RingPipe<int2> pipe;
+  pipe.slot0 = reinterpret_cast<int2*>(s_dyn) + threadIdx.x;
   const int32_t begin = w.seg_begin[cls * kNumJ + j_hi];
   const int32_t end = w.seg_end[cls * kNumJ + j_lo];
   int32_t* head = w.heads + head_id;
@@ -278,7 +281,8 @@ __global__ void __launch_bounds__(kLaneThreads, 4)
       o = lane_pair_p16<R, QSTAGE>(pr, valid, sc, s_prof, *reinterpret_cast<Ring<true>*>(&ring),
                                    mparam, qs);
     else
-      o = lane_pair_i32<R>(pr, valid, sc, s_prof, *reinterpret_cast<Ring<false>*>(&ring), mparam);
+      o = lane_pair_i32<R, GRING>(pr, valid, sc, s_prof, *reinterpret_cast<Ring<false>*>(&ring),
+                                  mparam, pipe);
     if (valid)
       write_result(b, k, o.score, o.qle, o.tle, o.gscore, o.gtle, o.max_off, XT_OK, o.cells);
   }
@@ -595,11 +599,15 @@ size_t lane_stage_bytes(int j_hi) {
   return j_hi <= kLaneStageJMax ? (size_t)kLaneThreads << j_hi : 0;
 }
 
+size_t lane_pipe_bytes(int cls, bool global_ring) {
+  return (global_ring && cls != CLS_PACKED) ? (size_t)kLaneThreads * kPipeD * sizeof(int2) : 0;
+}
+
 template <int R, bool PACKED, bool GRING, bool QSTAGE>
 static cudaError_t launch_lane_t(const Batch* b, const Score& sc, const Work& w, const Launch& L,
                                  int head_id, void* gring, cudaStream_t stream) {
   const size_t smem = (GRING ? 0 : kLaneThreads * lane_ring_bytes(L.cls, L.rs_log2)) +
-                      (QSTAGE ? lane_stage_bytes(L.j_hi) : 0);
+                      (QSTAGE ? lane_stage_bytes(L.j_hi) : 0) + lane_pipe_bytes(L.cls, GRING);
   auto kern = k_lane<R, PACKED, GRING, QSTAGE>;
   cudaError_t e = raise_smem_limit(kern, smem);
   if (e != cudaSuccess) return e;

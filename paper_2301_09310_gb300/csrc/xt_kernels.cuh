@@ -103,6 +103,8 @@ size_t queue_smem_bytes(int P, int rs_log2);
 size_t lane_ring_bytes(int cls, int rs_log2);
 // Query staging bytes per CTA of a one-lane launch whose longest bucket is j_hi (0: none).
 size_t lane_stage_bytes(int j_hi);
+// Ring-feed slot bytes per CTA of a one-lane launch (global rings of 32-bit pairs).
+size_t lane_pipe_bytes(int cls, bool global_ring);
 int max_smem_per_block_optin(int device);
 
 }  // namespace xt

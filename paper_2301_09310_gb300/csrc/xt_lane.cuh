@@ -75,6 +75,40 @@ struct Query {
   }
 };
 
+// The previous strip's bottom row, fed column by column through shared
+// memory for rings in a global slab: each lane keeps D slots, and the entry
+// of column c sits in slot c mod D.  A strip first starts copying its
+// columns lo .. lo+D-1 (cp.async, one commit group each); the step that
+// consumes column c waits until that copy has landed (at most D-1 younger
+// groups pending), reads the slot and refills it with column c+D.  Only
+// columns the strip consumes are copied, so no copy is in flight when the
+// strip ends; steps without a copy still commit an (empty) group to keep the
+// count.  The copies run D steps ahead of their use instead of the two that
+// registers allow.  Slot k of lane t sits at slot0 + k * kLaneThreads.
+constexpr int kPipeD = 16;
+
+template <typename T>
+struct RingPipe {
+  T* slot0;  // this lane's slot 0 (shared memory)
+  __device__ __forceinline__ T* slot(int32_t c) const {
+    return slot0 + (uint32_t)(c & (kPipeD - 1)) * kLaneThreads;
+  }
+  __device__ __forceinline__ void copy(const T* src, int32_t c) const {
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(slot(c));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst), "l"(src),
+                 "n"((int)sizeof(T))
+                 : "memory");
+  }
+  __device__ __forceinline__ void commit() const {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+  // the entry of column c, once its copy has landed
+  __device__ __forceinline__ T take(int32_t c) const {
+    asm volatile("cp.async.wait_group %0;" ::"n"(kPipeD - 1) : "memory");
+    return *slot(c);
+  }
+};
+
 // Unrolling of the fast-step loop of the packed engine (a tuning knob of the
 // build: the loop body is large, so unrolling trades register renaming of
 // the pipelined values against instruction-cache footprint).
@@ -123,10 +157,10 @@ __device__ __forceinline__ void lane_step_i32(int32_t (&Hl)[R], int32_t (&HAl)[R
 // Extend the pairs of one warp, one pair per lane, 32-bit (requires h0 +
 // match*min(qlen,tlen) <= 32767 and qlen <= 65535 for the row key).  Lanes
 // walk their strips in lockstep, as in the packed form.
-template <int R>
+template <int R, bool PIPE>
 __device__ __forceinline__ Outcome lane_pair_i32(const Pair& pr, bool valid, const Score& sc,
                                                  const uint32_t* s_prof, const Ring<false>& ring,
-                                                 int32_t mc) {
+                                                 int32_t mc, const RingPipe<int2>& pipe) {
   const int32_t qlen = pr.qlen, tlen = pr.tlen, h0 = pr.h0;
   const int32_t alpha = sc.alpha, beta = sc.beta, w = sc.w;
   const uint32_t nnnn = sc.nnnn;
@@ -175,15 +209,37 @@ __device__ __forceinline__ Outcome lane_pair_i32(const Pair& pr, bool valid, con
     const int32_t qlast = max(qlen - 1, 0);
     uint32_t code_n = live ? clamp_code(__ldg(pr.q + min(lo + 1, qlast))) : 0u;
     uint32_t prof_c = s_prof[live ? clamp_code(__ldg(pr.q + lo)) : 0u];
-    int2 ring_c = live ? ring.at(lo) : make_int2(0, 0);
-    int2 ring_n1 = live ? ring.at(lo + 1) : make_int2(0, 0);
+    int2 ring_c = make_int2(0, 0), ring_n1 = make_int2(0, 0);
+    // the last column the strip consumes a ring entry of: its steps end at
+    // column lo + nmax - 1, and the previous strip wrote up to hi_prev
+    const int32_t last_c = min(hi_prev, lo + nmax - 1);
+    if (PIPE) {
+      if (i0 > 0) {  // the first strip reads row -1, not the ring
+#pragma unroll
+        for (int k = 0; k < kPipeD; ++k) {
+          if (live && lo + k <= last_c) pipe.copy(&ring.at(lo + k), lo + k);
+          pipe.commit();
+        }
+      }
+    } else {
+      ring_c = live ? ring.at(lo) : make_int2(0, 0);
+      ring_n1 = live ? ring.at(lo + 1) : make_int2(0, 0);
+    }
+    // the entry of column c, and the copy of column c + kPipeD into its slot
+    auto feed = [&](int32_t c) -> int2 {
+      const int2 v = pipe.take(c);
+      if (live && c + kPipeD <= last_c) pipe.copy(&ring.at(c + kPipeD), c + kPipeD);
+      pipe.commit();
+      return v;
+    };
     auto slow_step = [&](int32_t s) {
       const int32_t c = lo + s;
       const bool act = live && c <= hi;
       const uint32_t code_nn = act ? clamp_code(__ldg(pr.q + min(c + 2, qlast))) : 0u;
       const uint32_t prof_n = s_prof[code_n];
-      const int2 ring_n2 = act ? ring.at(c + 2) : make_int2(0, 0);
+      const int2 ring_n2 = (!PIPE && act) ? ring.at(c + 2) : make_int2(0, 0);
       int32_t Hup = 0, Fup = 0;
+      if (i0 > 0 && PIPE) ring_c = feed(c);
       if (act) {
         if (i0 == 0) {
           Hup = row_m1(c, h0, sc);
@@ -210,12 +266,13 @@ __device__ __forceinline__ Outcome lane_pair_i32(const Pair& pr, bool valid, con
       const int32_t c = lo + s;
       const uint32_t code_nn = live ? clamp_code(__ldg(pr.q + min(c + 2, qlast))) : 0u;
       const uint32_t prof_n = s_prof[code_n];
-      const int2 ring_n2 = ring.at(c + 2);
+      const int2 ring_n2 = PIPE ? make_int2(0, 0) : ring.at(c + 2);
       int32_t Hup, Fup;
       if (i0 == 0) {
         Hup = row_m1(c, h0, sc);
         Fup = 0;
       } else {
+        if (PIPE) ring_c = feed(c);
         Hup = ring_c.x;
         Fup = ring_c.y;
       }
