@@ -76,8 +76,9 @@ struct Query {
 };
 
 // The previous strip's bottom row, fed column by column through shared
-// memory for rings in a global slab: each lane keeps D slots, and the entry
-// of column c sits in slot c mod D.  A strip first starts copying its
+// memory for rings in a global slab: each lane keeps D = 8 slots (measured
+// on c4_long: 8 beat 16 and 32, whose larger footprint takes L1 capacity),
+// and the entry of column c sits in slot c mod D.  A strip first starts copying its
 // columns lo .. lo+D-1 (cp.async, one commit group each); the step that
 // consumes column c waits until that copy has landed (at most D-1 younger
 // groups pending), reads the slot and refills it with column c+D.  Only
@@ -85,7 +86,7 @@ struct Query {
 // strip ends; steps without a copy still commit an (empty) group to keep the
 // count.  The copies run D steps ahead of their use instead of the two that
 // registers allow.  Slot k of lane t sits at slot0 + k * kLaneThreads.
-constexpr int kPipeD = 16;
+constexpr int kPipeD = 8;
 
 template <typename T>
 struct RingPipe {
