@@ -92,6 +92,9 @@ def parse_args():
                     help="auto: autotune the workload's length buckets before warm-up")
     ap.add_argument("--streams", type=int, default=0,
                     help="streams the extension kernels of a call fork onto (0: library default)")
+    ap.add_argument("--schedule", default="",
+                    help="P,R: one forced schedule for every bucket (profiling a kernel on a "
+                         "subset of a workload); default: the count-aware plan")
     ap.add_argument("--serve-slots", type=int, default=3)
     ap.add_argument("--serve-batch-mib", type=int, default=256,
                     help="staged bytes per batch (the slot capacity), MiB")
@@ -420,10 +423,12 @@ def run_xt(args):
     ctx = xt.Context(local)
     if args.streams:
         ctx.set_streams(args.streams)
+    if args.schedule:
+        ctx.set_schedule(*(int(x) for x in args.schedule.split(",")))
     stream = torch.cuda.current_stream(dev)
     tuning = None
     j_max = max(5, int(np.ceil(np.log2(int(b.q_len.max()) + 2))))
-    if args.tune == "auto":
+    if args.tune == "auto" and not args.schedule:
         # tune the workload's buckets, then keep the tuned table only if it
         # beats the built-in rule on the workload itself (the tuner's trials
         # are synthetic and one bucket at a time)
