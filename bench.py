@@ -42,18 +42,20 @@ SMS, MAX_MHZ = 152, 2070.0
 # Algorithmic instructions of one cell update (one 32-bit cell, or two cells
 # in the packed 16-bit form), with the fused DPX forms native on sm_103a:
 # on the integer ALU pipe S (byte permute), the anchored diagonal's add-min,
-# E and F (add-max with relu each), H (3-way max), H - alpha and the row key's
-# max: 7; on the multiply-add pipe the anchoring multiplier D * 2^k and the
-# row key H * 64 + step (H * 65536 + j in 32-bit): 2.
-ALU_OPS_PER_UPDATE, MAD_OPS_PER_UPDATE = 7, 2
+# E and F (add-max with relu each), H (3-way max) and the row key's max: 6;
+# on the multiply-add pipe the anchoring multiplier D * 2^k, the row key
+# H * 64 + step (H * 65536 + j in 32-bit) and H - alpha (a packed add issues
+# there, per the pipe counters of the instruction probes): 3.
+ALU_OPS_PER_UPDATE, MAD_OPS_PER_UPDATE = 6, 3
 OPS_PER_UPDATE = ALU_OPS_PER_UPDATE + MAD_OPS_PER_UPDATE
 # BWA-MEM-compatible cell, 32-bit: S, M (add, select), E and F (M minus the
 # opening penalty, then add-max each), H (3-way max), the row key's max: 9 on
 # the ALU pipe, and the key's multiply-add on the other: 10
 BWA_ALU_OPS_PER_CELL, BWA_OPS_PER_CELL = 9, 10
 # instruction probes whose rate is the integer ALU pipe's (the kinds the
-# cell update issues there)
-ALU_PROBES = ("add.s16x2", "max3.s16x2", "addmax.relu.s16x2", "prmt", "max3.s32")
+# cell update issues there; ncu pipe counters put the packed add on the
+# multiply-add pipe instead)
+ALU_PROBES = ("max3.s16x2", "addmax.relu.s16x2", "prmt", "max3.s32")
 LANE_MAX_QLEN = 510  # one-lane (packed-capable) buckets: qlen + 2 <= 2^9
 WORKLOAD_TEXT = {
     "c1_tiny": "1,000 pairs, 100 bp queries, 116 bp targets, 2% sub / 0.2% indel",
@@ -252,7 +254,7 @@ def measure_int_rates(local):
             "ms": {k: round(ms, 4) for k, (_, ms) in raw.items()},
             "sm_mhz": mhz, "sms": sms, "clocks": clocks,
             "alu_pipe": max(per_clk[k] for k in ALU_PROBES),
-            "mad_pipe": per_clk["imad.u32"], "issue": per_clk["add.s16x2 + imul.u32 alternating"],
+            "mad_pipe": per_clk["imad.u32"], "issue": per_clk["max.s16x2 + imul.u32 alternating"],
             "cell_update_cells": per_clk["packed cell update (cells)"]}
 
 

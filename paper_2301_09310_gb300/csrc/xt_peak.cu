@@ -43,13 +43,13 @@ __device__ __forceinline__ uint32_t op_step(uint32_t a, uint32_t b, uint32_t c, 
     r = (uint32_t)__vimax3_s32((int)a, (int)b, (int)c);
   } else if constexpr (OP == XT_RATE_IMAD) {
     r = a * b + c;
-  } else {  // XT_RATE_MIX: a packed add and a multiply, alternating by chain
-    // (two-source instructions of the two integer pipes: three-source ones
-    // alternating are limited by register reads before the issue slots)
+  } else {  // XT_RATE_MIX: a packed max and a multiply, alternating by chain
+    // (two-source instructions of the two integer pipes, the ALU and the
+    // multiply-add pipe: the packed add issues to the multiply-add pipe too)
     if (k & 1) {
       r = a * b;
     } else {
-      asm("add.s16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+      asm("max.s16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
     }
   }
   return r;
