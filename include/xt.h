@@ -412,9 +412,10 @@ xt_status xt_shard_lpt(const int32_t* q_len, const int32_t* t_len, int32_t n_pai
  * instruction in independent chains on every SM (8 chains per thread, a full
  * SM of warps) and is timed with CUDA events after one warm-up launch; the
  * best of `reps` launches is returned: *units instructions (thread-level) in
- * *ms milliseconds.  XT_RATE_MIX alternates a packed max with a 32-bit
- * multiply, two-source instructions that issue to different pipes (the
- * integer ALU and the multiply-add pipe), so it measures the issue rate.  XT_RATE_CELL_P16 runs the packed cell update of
+ * *ms milliseconds.  XT_RATE_MIX interleaves a packed max (integer ALU
+ * pipe) and a packed add (multiply-add pipe) in every chain, two-source
+ * instructions of the two pipes, so it measures the issue rate (*units
+ * counts both).  XT_RATE_CELL_P16 runs the packed cell update of
  * the one-lane engine on registers (the engine's fast step, 16 cells per step
  * and thread); *units then counts cells.  Synchronous; allocates a few bytes
  * of device memory; XT_EINVAL for an unknown op or device.
@@ -426,7 +427,7 @@ xt_status xt_shard_lpt(const int32_t* q_len, const int32_t* t_len, int32_t n_pai
 #define XT_RATE_IADD3 4        /* 32-bit three-input add */
 #define XT_RATE_MAX3_32 5      /* 3-way 32-bit max */
 #define XT_RATE_IMAD 6         /* 32-bit multiply-add */
-#define XT_RATE_MIX 7          /* packed max and 32-bit multiply, alternating */
+#define XT_RATE_MIX 7          /* packed max and packed add, interleaved */
 #define XT_RATE_CELL_P16 8     /* the packed cell update (cells, not instructions) */
 xt_status xt_int_rate(int device, int op, int reps, int64_t* units, double* ms);
 

@@ -43,16 +43,16 @@ __device__ __forceinline__ uint32_t op_step(uint32_t a, uint32_t b, uint32_t c, 
     r = (uint32_t)__vimax3_s32((int)a, (int)b, (int)c);
   } else if constexpr (OP == XT_RATE_IMAD) {
     r = a * b + c;
-  } else {  // XT_RATE_MIX: a packed max and a multiply, alternating by chain
-    // (two-source instructions of the two integer pipes, the ALU and the
-    // multiply-add pipe: the packed add issues to the multiply-add pipe too)
-    if (k & 1) {
-      r = a * b;
-    } else {
-      asm("max.s16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
-    }
   }
   return r;
+}
+
+// XT_RATE_MIX: every chain takes a packed max (ALU pipe) into a and a packed
+// add (multiply-add pipe) into b per step, a = max(a, b), b = b + c; b moves
+// every step, so no run of maxes against a fixed operand can be folded.
+__device__ __forceinline__ void mix_step(uint32_t& a, uint32_t& b, uint32_t c) {
+  asm("max.s16x2 %0, %0, %1;" : "+r"(a) : "r"(b));
+  asm("add.s16x2 %0, %0, %1;" : "+r"(b) : "r"(c));
 }
 
 template <int OP>
@@ -70,7 +70,12 @@ __global__ void __launch_bounds__(kRateThreads) k_rate(uint32_t seed, int iters,
     for (int u = 0; u < kUnroll; ++u) {
 #pragma unroll
       for (int k = 0; k < kChains; ++k) {
-        a[k] = op_step<OP>(a[k], b[k], c[k], k);
+        if constexpr (OP == XT_RATE_MIX) {
+          mix_step(a[k], b[k], c[k]);
+          opaque(b[k]);
+        } else {
+          a[k] = op_step<OP>(a[k], b[k], c[k], k);
+        }
         opaque(a[k]);
       }
     }
@@ -166,7 +171,9 @@ extern "C" xt_status xt_int_rate(int device, int op, int reps, int64_t* units, d
   const int threads = cell ? xt::kLaneThreads : kRateThreads;
   const int grid = sms * (cell ? 4 : 2048 / kRateThreads);
   const int iters = cell ? 20000 : 8192;
-  const int64_t per_thread = cell ? (int64_t)iters * 16 : (int64_t)iters * kUnroll * kChains;
+  // the mix probe issues two instructions per chain step
+  const int64_t per_thread = cell ? (int64_t)iters * 16
+                                  : (int64_t)iters * kUnroll * kChains * (op == XT_RATE_MIX ? 2 : 1);
   uint32_t* sink = nullptr;
   cudaStream_t st = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
