@@ -86,6 +86,8 @@ def parse_args():
                     help="skip the BWA-MEM-compatible extension leg")
     ap.add_argument("--no-x2", action="store_true",
                     help="skip the equal-length 5,000-pair calls of the paper's kernel comparison")
+    ap.add_argument("--no-packed4", action="store_true",
+                    help="skip the same batch given as 4-bit codes (device-resident and e2e)")
     ap.add_argument("--no-c4", action="store_true",
                     help="skip the 250,000 long pairs of c4_long (w = 500, z-drop 400)")
     ap.add_argument("--serve-pairs", type=int, default=10_000_000,
@@ -558,6 +560,8 @@ def run_xt(args):
         res["bwa_compatible"] = bwa_leg(b, wl, args, local, stream, rates, run_mhz)
     if not args.no_e2e:
         res["e2e"] = e2e_leg(ctx, b, wl, args, dev, stream, world)
+    if not args.no_packed4 and world == 1:
+        res["packed4"] = packed4_leg(b, wl, args, local, stream, cells_step)
     if not args.no_x2 and world == 1:
         res["paper_x2"] = x2_leg(local, stream)
     if not args.no_c4 and world == 1 and args.workload != "c4_long":
@@ -645,6 +649,61 @@ def bwa_leg(b, wl, args, local, stream, rates, mhz):
                              kernel="whole call (classify, order, k_bwa)"),
             "scoring": list(sc.as_tuple()),
             "kernel": "k_bwa: one pair per group of 2..256 lanes, a row's live columns at a time, int32"}
+
+
+def packed4_leg(b, wl, args, local, stream, cells_step):
+    """The same batch as 4-bit codes, two per byte (xt_ctx_set_alphabet
+    XT_ALPHABET_PACKED4, the paper's 4-bit packing): device-resident calls
+    (each unpacks both buffers on the GPU first), and the host-buffer call,
+    which copies the packed bytes (half those of base codes) in chunks and
+    unpacks each chunk on the GPU as it arrives."""
+    import torch
+    import paper_2301_09310_gb300 as xt
+
+    dev = torch.device("cuda", local)
+    q4, t4 = xt.pack4(b.q_seq), xt.pack4(b.t_seq)
+    d = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in
+         (q4, b.q_off, b.q_len, t4, b.t_off, b.t_len, b.h0)]
+    ctx = xt.Context(local)
+    ctx.set_alphabet(xt.XT_ALPHABET_PACKED4)
+    out = torch.empty((b.n, 7), dtype=torch.int32, device=dev)
+    cells = torch.empty(b.n, dtype=torch.int64, device=dev)
+    for _ in range(3):
+        ctx.extend(*d, wl.scoring, out=out, cells=cells, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(3, min(args.steps, 10))
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.extend(*d, wl.scoring, out=out, cells=cells, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    same = int(cells.sum().item()) == cells_step
+    del d, out, cells
+
+    def pinned(a):
+        t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
+        t.numpy()[...] = a
+        return t.numpy()
+
+    h = [pinned(a) for a in (q4, b.q_off, b.q_len, t4, b.t_off, b.t_len, b.h0)]
+    hout = pinned(np.zeros((b.n, 7), np.int32))
+    hcells = pinned(np.zeros(b.n, np.int64))
+    ctx.extend_host(*h, wl.scoring, out=hout, cells=hcells, stream=stream)
+    ereps = max(1, min(args.steps, 5))
+    t = time.perf_counter()
+    for _ in range(ereps):
+        ctx.extend_host(*h, wl.scoring, out=hout, cells=hcells, stream=stream)
+    dt = (time.perf_counter() - t) / ereps
+    ctx.close()
+    return {"value": round(cells_step / (ms / 1e3) / 1e9, 3), "unit": "GCUPS",
+            "ms_per_step": round(ms, 4), "same_cells_as_codes": same,
+            "input": "4-bit codes, two per byte; unpacked on the GPU in each call",
+            "e2e": {"value": round(int(hcells.sum()) / dt / 1e9, 3), "unit": "GCUPS",
+                    "h2d_bytes_per_step": sum(int(a.nbytes) for a in h),
+                    "d2h_bytes_per_step": int(hout.nbytes + hcells.nbytes),
+                    "ms_per_step": round(dt * 1e3, 3),
+                    "api": "xt_extend_batch_host with XT_ALPHABET_PACKED4 (pinned host buffers)"}}
 
 
 def c4_leg(args, local, stream, rates, mhz):

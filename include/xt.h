@@ -317,11 +317,23 @@ xt_status xt_ctx_load_tuning(xt_ctx* ctx, const char* table_path);
  * elementwise pass that writes the base codes of both sequence buffers into
  * the context's workspace (q_bytes + t_bytes bytes, within its budget) and
  * extends from those.  Results are those of the same sequences given as
- * base codes.  (The allocation-free xt_extend_batch_static reads base codes
- * only.)
+ * base codes.
+ * XT_ALPHABET_PACKED4: base codes packed two to a byte, the paper's 4-bit
+ * packing (Sec. II-B, eight bases per 32-bit word): base p of a buffer is the
+ * low nibble of byte p / 2 when p is even and the high nibble when p is odd
+ * (0..3 = A, C, G, T, any other nibble N).  Offsets and lengths count bases;
+ * q_bytes / t_bytes are the buffers' sizes in bytes, so a buffer holds
+ * 2 * bytes bases.  A call first unpacks both buffers to one code per byte in
+ * the context's workspace (2 * (q_bytes + t_bytes) bytes, within its budget);
+ * xt_extend_batch_host copies the packed bytes, half those of base codes, and
+ * unpacks each chunk's bytes as they arrive.  Results are those of the same
+ * sequences given as base codes.
+ * (The allocation-free xt_extend_batch_static reads base codes only, and the
+ * serving loop takes base codes or ASCII: XT_EINVAL at xt_serve_create.)
  */
 #define XT_ALPHABET_CODES 0
 #define XT_ALPHABET_ASCII 1
+#define XT_ALPHABET_PACKED4 2
 xt_status xt_ctx_set_alphabet(xt_ctx* ctx, int alphabet);
 
 /* XT_OK if the scoring record is within the ranges above, else XT_EINVAL. */
@@ -514,7 +526,8 @@ typedef struct {
                                thread included (0: a quarter of the cores, <= 8) */
   const char* tuning_path;  /* a table written by xt_autotune, loaded into every
                                slot's context (NULL: built-in schedules) */
-  int32_t alphabet;         /* XT_ALPHABET_CODES (0) or XT_ALPHABET_ASCII */
+  int32_t alphabet;         /* XT_ALPHABET_CODES (0) or XT_ALPHABET_ASCII (not
+                               XT_ALPHABET_PACKED4: XT_EINVAL) */
 } xt_serve_config;
 
 /* Latency stamps of one request, ns on CLOCK_MONOTONIC (see xt_now_ns). */

@@ -263,7 +263,19 @@ def xt_ctx_load_tuning(ctx: int, table_path: str) -> int:
     return load_library().xt_ctx_load_tuning(ctypes.c_void_p(ctx), table_path.encode())
 
 
-XT_ALPHABET_CODES, XT_ALPHABET_ASCII = 0, 1
+XT_ALPHABET_CODES, XT_ALPHABET_ASCII, XT_ALPHABET_PACKED4 = 0, 1, 2
+
+
+def pack4(codes):
+    """Host-side packing of base codes into the 4-bit layout of
+    XT_ALPHABET_PACKED4: base p is the low nibble of byte p // 2 when p is
+    even and the high nibble when p is odd (codes above 15 become 15, N).
+    Offsets and lengths of the pairs stay in bases."""
+    import numpy as np
+    c = np.minimum(np.asarray(codes, np.uint8), 15)
+    if c.size % 2:
+        c = np.concatenate([c, np.zeros(1, np.uint8)])
+    return (c[0::2] | (c[1::2] << 4)).astype(np.uint8)
 
 
 def xt_ctx_set_alphabet(ctx: int, alphabet: int) -> int:
@@ -541,7 +553,8 @@ class Context:
         self._check(xt_ctx_load_tuning(self.handle, table_path), "xt_ctx_load_tuning")
 
     def set_alphabet(self, alphabet: int):
-        """XT_ALPHABET_CODES (base codes 0..3) or XT_ALPHABET_ASCII (raw letters)."""
+        """XT_ALPHABET_CODES (base codes 0..3), XT_ALPHABET_ASCII (raw letters) or
+        XT_ALPHABET_PACKED4 (two 4-bit codes per byte, see pack4)."""
         self._check(xt_ctx_set_alphabet(self.handle, alphabet), "xt_ctx_set_alphabet")
 
     def set_streams(self, branches: int):

@@ -101,18 +101,28 @@ xt_status xt::ctx_alloc(xt_ctx* ctx, void** p, size_t* have, size_t want) {
   return dev_alloc(ctx, p, have, want);
 }
 
-xt_status xt::ctx_codes(xt_ctx* ctx, const uint8_t** q_seq, int64_t q_bytes,
-                        const uint8_t** t_seq, int64_t t_bytes, cudaStream_t stream) {
-  if (ctx->alphabet != XT_ALPHABET_ASCII) return XT_OK;
-  const size_t qa = align_up((size_t)q_bytes);
-  xt_status s = dev_alloc(ctx, &ctx->conv, &ctx->conv_bytes, qa + (size_t)t_bytes + kAlign);
+xt_status xt::ctx_codes(xt_ctx* ctx, const uint8_t** q_seq, int64_t* q_bytes,
+                        const uint8_t** t_seq, int64_t* t_bytes, cudaStream_t stream) {
+  if (ctx->alphabet == XT_ALPHABET_CODES) return XT_OK;
+  const bool packed = ctx->alphabet == XT_ALPHABET_PACKED4;
+  const int64_t qn = packed ? 2 * *q_bytes : *q_bytes, tn = packed ? 2 * *t_bytes : *t_bytes;
+  const size_t qa = align_up((size_t)qn);
+  xt_status s = dev_alloc(ctx, &ctx->conv, &ctx->conv_bytes, qa + (size_t)tn + kAlign);
   if (s != XT_OK) return s;
   uint8_t* cq = static_cast<uint8_t*>(ctx->conv);
-  cudaError_t e = launch_ascii_codes(*q_seq, cq, q_bytes, ctx->num_sms, stream);
-  if (e == cudaSuccess) e = launch_ascii_codes(*t_seq, cq + qa, t_bytes, ctx->num_sms, stream);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "ASCII conversion");
+  cudaError_t e;
+  if (packed) {
+    e = launch_unpack4(*q_seq, cq, 0, *q_bytes, ctx->num_sms, stream);
+    if (e == cudaSuccess) e = launch_unpack4(*t_seq, cq + qa, 0, *t_bytes, ctx->num_sms, stream);
+  } else {
+    e = launch_ascii_codes(*q_seq, cq, *q_bytes, ctx->num_sms, stream);
+    if (e == cudaSuccess) e = launch_ascii_codes(*t_seq, cq + qa, *t_bytes, ctx->num_sms, stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, packed ? "4-bit unpacking" : "ASCII conversion");
   *q_seq = cq;
   *t_seq = cq + qa;
+  *q_bytes = qn;
+  *t_bytes = tn;
   return XT_OK;
 }
 
@@ -659,9 +669,9 @@ xt_status run_begin(xt_ctx* ctx, bool plain, const uint8_t* q_seq, int64_t q_byt
   if (s != XT_OK) return s;
   ctx->match = scr->match;
   ctx->plan_small = false;
-  // raw reads: an elementwise pass turns the letters into base codes in the
-  // context's workspace, and the call reads those
-  s = ctx_codes(ctx, &q_seq, q_bytes, &t_seq, t_bytes, stream);
+  // raw reads or 4-bit codes: an elementwise pass writes one base code per
+  // byte into the context's workspace, and the call reads those
+  s = ctx_codes(ctx, &q_seq, &q_bytes, &t_seq, &t_bytes, stream);
   if (s != XT_OK) return s;
   // this call's arguments go to the device descriptor through a one-thread
   // kernel (a kernel parameter, not a copy: a host-to-device copy here would
@@ -801,6 +811,14 @@ xt_status run(xt_ctx* ctx, bool plain, const uint8_t* q_seq, int64_t q_bytes, co
   }
   return run_finish(ctx);
 }
+
+// Both-direction extension of seeds whose sequences are base codes (below).
+xt_status seeds_codes(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_bytes, const int64_t* q_off,
+                      const int32_t* q_len, const uint8_t* t_seq, int64_t t_bytes,
+                      const int64_t* t_off, const int32_t* t_len, const int32_t* q_beg,
+                      const int32_t* t_beg, const int32_t* seed_len, const int32_t* h0,
+                      int32_t n_pairs, const xt_scoring* sc, xt_result* left, xt_result* right,
+                      int64_t* left_cells, int64_t* right_cells, cudaStream_t st);
 
 }  // namespace
 
@@ -955,6 +973,34 @@ xt_status xt_extend_seeds(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_bytes, co
   if (n_pairs == 0) return XT_OK;
   cudaStream_t st = (cudaStream_t)stream;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, XT_ECUDA, "cudaSetDevice");
+  // 4-bit codes are unpacked first: the reversed prefixes are copied base by
+  // base, and both sides then read one code per byte
+  if (ctx->alphabet == XT_ALPHABET_PACKED4) {
+    s = ctx_codes(ctx, &q_seq, &q_bytes, &t_seq, &t_bytes, st);
+    if (s != XT_OK) return s;
+    ctx->alphabet = XT_ALPHABET_CODES;
+    s = seeds_codes(ctx, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off, t_len, q_beg, t_beg,
+                    seed_len, h0, n_pairs, sc, left, right, left_cells, right_cells, st);
+    ctx->alphabet = XT_ALPHABET_PACKED4;
+    return s;
+  }
+  return seeds_codes(ctx, q_seq, q_bytes, q_off, q_len, t_seq, t_bytes, t_off, t_len, q_beg, t_beg,
+                     seed_len, h0, n_pairs, sc, left, right, left_cells, right_cells, st);
+}
+
+}  // extern "C"
+
+namespace {
+
+// Both-direction extension of checked, non-empty seed batches (the caller
+// holds the context's lock).
+xt_status seeds_codes(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_bytes, const int64_t* q_off,
+                      const int32_t* q_len, const uint8_t* t_seq, int64_t t_bytes,
+                      const int64_t* t_off, const int32_t* t_len, const int32_t* q_beg,
+                      const int32_t* t_beg, const int32_t* seed_len, const int32_t* h0,
+                      int32_t n_pairs, const xt_scoring* sc, xt_result* left, xt_result* right,
+                      int64_t* left_cells, int64_t* right_cells, cudaStream_t st) {
+  xt_status s = XT_OK;
   // workspace: per-seed arrays and the block sums
   const size_t n = (size_t)n_pairs;
   const size_t nb = (n + 1023) / 1024;
@@ -1010,6 +1056,10 @@ xt_status xt_extend_seeds(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_bytes, co
              sw.rt_len, sw.rh0, n_pairs, sc, right, right_cells, st);
 }
 
+}  // namespace
+
+extern "C" {
+
 xt_status xt_extend_batch_host(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_bytes,
                                const int64_t* q_off, const int32_t* q_len, const uint8_t* t_seq,
                                int64_t t_bytes, const int64_t* t_off, const int32_t* t_len,
@@ -1025,9 +1075,15 @@ xt_status xt_extend_batch_host(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_byte
   cudaStream_t st = (cudaStream_t)stream;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, XT_ECUDA, "cudaSetDevice");
   const size_t n = (size_t)n_pairs;
+  // 4-bit codes arrive packed (half the bytes of base codes) and are unpacked
+  // on the device, chunk by chunk below
+  const bool packed = ctx->alphabet == XT_ALPHABET_PACKED4;
+  const int64_t qn = packed ? 2 * q_bytes : q_bytes, tn = packed ? 2 * t_bytes : t_bytes;
   size_t off = 0;
   const size_t o_q = off; off = align_up(off + (size_t)q_bytes);
   const size_t o_t = off; off = align_up(off + (size_t)t_bytes);
+  const size_t o_qc = off; off = align_up(off + (packed ? (size_t)qn : 0));
+  const size_t o_tc = off; off = align_up(off + (packed ? (size_t)tn : 0));
   const size_t o_qo = off; off = align_up(off + 8 * n);
   const size_t o_to = off; off = align_up(off + 8 * n);
   const size_t o_ql = off; off = align_up(off + 4 * n);
@@ -1054,7 +1110,7 @@ xt_status xt_extend_batch_host(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_byte
   // many pairs: chunks of at least kChunkPairs pairs, each extended as soon as
   // the sequence bytes it reads are on the device, while the copy stream
   // brings the next chunk's bytes and takes the finished chunks' results back
-  const int chunks = ctx->alphabet != XT_ALPHABET_CODES
+  const int chunks = ctx->alphabet == XT_ALPHABET_ASCII
                          ? 1
                          : (int)std::min<int64_t>(kMaxChunks, (int64_t)n_pairs / kChunkPairs);
   if (chunks <= 1) {
@@ -1091,7 +1147,7 @@ xt_status xt_extend_batch_host(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_byte
   if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev[1], 0);
   if (e == cudaSuccess) e = cudaMemsetAsync(dends, 0, 16 * kMaxChunks, st);
   if (e == cudaSuccess)
-    e = launch_chunk_ends(dqo, dql, dto, dtl, n_pairs, cp, q_bytes, t_bytes, dends, st);
+    e = launch_chunk_ends(dqo, dql, dto, dtl, n_pairs, cp, qn, tn, dends, st);
   unsigned long long* ends = reinterpret_cast<unsigned long long*>(ctx->seg_host + kSegHostChunkEnds);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(ends, dends, 16 * kMaxChunks, cudaMemcpyDeviceToHost, st);
@@ -1104,23 +1160,39 @@ xt_status xt_extend_batch_host(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_byte
     need_q[k] = std::max<int64_t>(k ? need_q[k - 1] : 0, (int64_t)ends[2 * k]);
     need_t[k] = std::max<int64_t>(k ? need_t[k - 1] : 0, (int64_t)ends[2 * k + 1]);
   }
+  // bases [0, need) of a buffer are its bytes [0, need) as codes, or
+  // [0, ceil(need / 2)) when packed; a packed chunk is unpacked on the copy
+  // stream as soon as its bytes are there
+  auto bytes_of = [&](int64_t bases) { return packed ? (bases + 1) / 2 : bases; };
   for (int k = 0; k < chunks && e == cudaSuccess; ++k) {
-    const int64_t q0 = k ? need_q[k - 1] : 0, t0 = k ? need_t[k - 1] : 0;
-    h2d(o_q + (size_t)q0, q_seq + q0, (size_t)(need_q[k] - q0), cs);
-    h2d(o_t + (size_t)t0, t_seq + t0, (size_t)(need_t[k] - t0), cs);
+    const int64_t q0 = k ? bytes_of(need_q[k - 1]) : 0, t0 = k ? bytes_of(need_t[k - 1]) : 0;
+    const int64_t q1 = bytes_of(need_q[k]), t1 = bytes_of(need_t[k]);
+    h2d(o_q + (size_t)q0, q_seq + q0, (size_t)(q1 - q0), cs);
+    h2d(o_t + (size_t)t0, t_seq + t0, (size_t)(t1 - t0), cs);
+    if (packed && e == cudaSuccess) {
+      e = launch_unpack4((const uint8_t*)(d + o_q), (uint8_t*)(d + o_qc), q0, q1, ctx->num_sms, cs);
+      if (e == cudaSuccess)
+        e = launch_unpack4((const uint8_t*)(d + o_t), (uint8_t*)(d + o_tc), t0, t1, ctx->num_sms,
+                           cs);
+    }
     if (e == cudaSuccess) e = cudaEventRecord(ev[2 + k], cs);
   }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "host to device copy");
+  // the chunks read the unpacked codes (the context's alphabet is codes for them)
+  const uint8_t* cq = (const uint8_t*)(d + (packed ? o_qc : o_q));
+  const uint8_t* ct = (const uint8_t*)(d + (packed ? o_tc : o_t));
+  const int alphabet = ctx->alphabet;
+  ctx->alphabet = XT_ALPHABET_CODES;
   for (int k = 0; k < chunks; ++k) {
     const int32_t p0 = (int32_t)std::min<int64_t>((int64_t)k * cp, n_pairs);
     const int32_t p1 = (int32_t)std::min<int64_t>((int64_t)(k + 1) * cp, n_pairs);
     if (p1 <= p0) continue;
     e = cudaStreamWaitEvent(st, ev[2 + k], 0);
     if (e != cudaSuccess) break;
-    s = run(ctx, false, (const uint8_t*)(d + o_q), q_bytes, dqo + p0, dql + p0,
-            (const uint8_t*)(d + o_t), t_bytes, dto + p0, dtl + p0, dh0 + p0, p1 - p0, sc,
-            dout + p0, dcells ? dcells + p0 : nullptr, st);
+    s = run(ctx, false, cq, qn, dqo + p0, dql + p0, ct, tn, dto + p0, dtl + p0, dh0 + p0, p1 - p0,
+            sc, dout + p0, dcells ? dcells + p0 : nullptr, st);
     if (s != XT_OK) {
+      ctx->alphabet = alphabet;
       cudaStreamSynchronize(cs);
       cudaStreamSynchronize(st);
       return s;
@@ -1135,6 +1207,7 @@ xt_status xt_extend_batch_host(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_byte
                           cudaMemcpyDeviceToHost, cs);
     if (e != cudaSuccess) break;
   }
+  ctx->alphabet = alphabet;
   cudaError_t e2 = cudaStreamSynchronize(cs);
   if (e == cudaSuccess) e = e2;
   e2 = cudaStreamSynchronize(st);
@@ -1201,7 +1274,9 @@ xt_status xt_ctx_get_bucket_schedule_for(xt_ctx* ctx, int w, int j, int batch_cl
 }
 
 xt_status xt_ctx_set_alphabet(xt_ctx* ctx, int alphabet) {
-  if (!ctx || (alphabet != XT_ALPHABET_CODES && alphabet != XT_ALPHABET_ASCII)) return XT_EINVAL;
+  if (!ctx || (alphabet != XT_ALPHABET_CODES && alphabet != XT_ALPHABET_ASCII &&
+               alphabet != XT_ALPHABET_PACKED4))
+    return XT_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   ctx->alphabet = alphabet;
   return XT_OK;

@@ -666,7 +666,7 @@ extern "C" xt_status xt_extend_batch_bwa(xt_ctx* ctx, const uint8_t* q_seq, int6
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return ctx_cuda_fail(ctx, e, "cudaSetDevice");
-  xt_status s = ctx_codes(ctx, &q_seq, q_bytes, &t_seq, t_bytes, st);
+  xt_status s = ctx_codes(ctx, &q_seq, &q_bytes, &t_seq, &t_bytes, st);
   if (s != XT_OK) return s;
   // workspace: class bytes, order, counters
   const size_t n = (size_t)n_pairs;

@@ -63,10 +63,11 @@ xt_status ctx_fail(struct ::xt_ctx* ctx, xt_status s, const char* msg);
 xt_status ctx_cuda_fail(struct ::xt_ctx* ctx, cudaError_t e, const char* where);
 // Grow *p (holding *have bytes) to at least `want` bytes within the budget.
 xt_status ctx_alloc(struct ::xt_ctx* ctx, void** p, size_t* have, size_t want);
-// With the ASCII alphabet, convert both sequence buffers to base codes in the
-// context's workspace and point *q_seq / *t_seq at them (no-op otherwise).
-xt_status ctx_codes(struct ::xt_ctx* ctx, const uint8_t** q_seq, int64_t q_bytes,
-                    const uint8_t** t_seq, int64_t t_bytes, cudaStream_t stream);
+// With the ASCII or the 4-bit alphabet, convert both sequence buffers to one
+// base code per byte in the context's workspace, point *q_seq / *t_seq at
+// them and set *q_bytes / *t_bytes to their sizes in bases (no-op for codes).
+xt_status ctx_codes(struct ::xt_ctx* ctx, const uint8_t** q_seq, int64_t* q_bytes,
+                    const uint8_t** t_seq, int64_t* t_bytes, cudaStream_t stream);
 
 // Host-buffer calls of many pairs run in chunks of pairs whose sequence
 // bytes are copied while earlier chunks extend (xt_extend_batch_host).

@@ -356,6 +356,61 @@ cudaError_t launch_ascii_codes(const uint8_t* in, uint8_t* out, int64_t n, int n
   return cudaGetLastError();
 }
 
+// ------------------------------------------------ 4-bit codes -> bytes
+// Two 4-bit codes per byte (base 2k in the low nibble of byte k, base 2k+1 in
+// the high nibble) to one code per byte.  A thread expands one 32-bit word
+// (eight bases) into two: the low nibbles of its bytes are bases 0, 2, 4, 6,
+// the high nibbles 1, 3, 5, 7, interleaved back by two byte permutes.
+// Bytes [b0, b1) of `in` become bytes [2 b0, 2 b1) of `out`; grid-stride.
+__device__ __forceinline__ void unpack_word(uint32_t w, uint32_t* lo, uint32_t* hi) {
+  const uint32_t ev = w & 0x0F0F0F0Fu, od = (w >> 4) & 0x0F0F0F0Fu;
+  uint32_t a, b;
+  asm("prmt.b32 %0, %1, %2, 0x5140;" : "=r"(a) : "r"(ev), "r"(od));
+  asm("prmt.b32 %0, %1, %2, 0x7362;" : "=r"(b) : "r"(ev), "r"(od));
+  *lo = a;
+  *hi = b;
+}
+
+__global__ void k_unpack4(const uint8_t* __restrict__ in, uint8_t* __restrict__ out, int64_t b0,
+                          int64_t b1) {
+  // word-aligned middle: whole 32-bit words of `in` (out is then 8-byte aligned
+  // whenever both buffers start on 8-byte boundaries)
+  const bool words = ((reinterpret_cast<uintptr_t>(in) & 3u) == 0) &&
+                     ((reinterpret_cast<uintptr_t>(out) & 7u) == 0);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t m0 = b0, m1 = b0;
+  if (words) {
+    m0 = (b0 + 3) & ~(int64_t)3;
+    m1 = b1 & ~(int64_t)3;
+    if (m1 < m0) m1 = m0;
+    for (int64_t k = m0 / 4 + t; k < m1 / 4; k += stride) {
+      uint32_t lo, hi;
+      unpack_word(__ldg(reinterpret_cast<const uint32_t*>(in) + k), &lo, &hi);
+      reinterpret_cast<uint2*>(out)[k] = make_uint2(lo, hi);
+    }
+  }
+  // the ragged ends (or everything, unaligned) byte by byte
+  auto one = [&](int64_t k) {
+    const uint32_t v = in[k];
+    out[2 * k] = (uint8_t)(v & 15u);
+    out[2 * k + 1] = (uint8_t)(v >> 4);
+  };
+  for (int64_t k = b0 + t; k < (words ? m0 : b1); k += stride) one(k);
+  if (words)
+    for (int64_t k = m1 + t; k < b1; k += stride) one(k);
+}
+
+cudaError_t launch_unpack4(const uint8_t* in, uint8_t* out, int64_t b0, int64_t b1, int num_sms,
+                           cudaStream_t stream) {
+  if (b1 <= b0) return cudaSuccess;
+  const int T = 256;
+  const int64_t want = ((b1 - b0) / 4 + T - 1) / T + 1;
+  const int grid = (int)(want < (int64_t)num_sms * 8 ? want : (int64_t)num_sms * 8);
+  k_unpack4<<<grid, T, 0, stream>>>(in, out, b0, b1);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------ both-direction seeds
 // Seed k: an exact match of seed_len[k] bases at query q_beg[k] and target
 // t_beg[k].  Left lengths are the prefixes before the seed, right views the

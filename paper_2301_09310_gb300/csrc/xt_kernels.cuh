@@ -74,6 +74,10 @@ cudaError_t launch_lane(const Batch* bd, const Score& sc, const Work& w, const L
 // ASCII letters to base codes (A/C/G/T either case -> 0..3, else 4), n bytes.
 cudaError_t launch_ascii_codes(const uint8_t* in, uint8_t* out, int64_t n, int num_sms,
                                cudaStream_t stream);
+// 4-bit codes, two per byte, to one code per byte: bytes [b0, b1) of `in`
+// become bytes [2 b0, 2 b1) of `out`.
+cudaError_t launch_unpack4(const uint8_t* in, uint8_t* out, int64_t b0, int64_t b1, int num_sms,
+                           cudaStream_t stream);
 // Both-direction extension of seeds: device workspace (carved by the host).
 struct SeedWork {
   int32_t *lq_len, *lt_len;   // left (reversed prefix) lengths, -1: invalid seed

@@ -438,6 +438,8 @@ xt_status xt_serve_create(xt_server** out, int device, const xt_serve_config* cf
       cfg.max_batch_pairs > kMaxBatchPairsCap || cfg.max_batch_bytes < 4096 ||
       cfg.max_queued_bytes < 1 || cfg.gather_threads < 1 || cfg.gather_threads > kMaxGatherThreads)
     return XT_EINVAL;
+  // requests are gathered byte by byte: codes or ASCII letters, not 4-bit codes
+  if (cfg.alphabet != XT_ALPHABET_CODES && cfg.alphabet != XT_ALPHABET_ASCII) return XT_EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return XT_EINVAL;
   if (cudaSetDevice(device) != cudaSuccess) return XT_ECUDA;

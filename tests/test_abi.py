@@ -55,3 +55,21 @@ def test_null_context_is_rejected(lib):
     assert lib.xt_ctx_create(None, 0, 0) == 1
     assert lib.xt_ctx_destroy(None) == 1
     assert lib.xt_ctx_set_schedule(None, 4, 8) == 1
+
+
+def test_pack4_layout():
+    # base p is the low nibble of byte p // 2 when p is even, the high one when odd
+    import numpy as np
+    codes = np.array([0, 1, 2, 3, 4, 3, 2], np.uint8)
+    packed = xt.pack4(codes)
+    assert packed.tolist() == [0x10, 0x32, 0x34, 0x02]
+    unpacked = np.stack([packed & 15, packed >> 4], axis=1).reshape(-1)[:codes.size]
+    assert np.array_equal(unpacked, codes)
+    assert xt.pack4(np.array([200], np.uint8)).tolist() == [15]
+
+
+def test_alphabet_values_match_header():
+    src = open(os.path.join(ROOT, "include", "xt.h")).read()
+    for name in ("XT_ALPHABET_CODES", "XT_ALPHABET_ASCII", "XT_ALPHABET_PACKED4"):
+        m = re.search(rf"#define {name} (\d+)", src)
+        assert m and int(m.group(1)) == getattr(xt, name)

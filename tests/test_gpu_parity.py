@@ -351,3 +351,75 @@ def test_ascii_reads(ctx, shift):
                             f"ascii shift={shift} plain={plain}")
     finally:
         other.close()
+
+
+def _odd_start(batch):
+    """The same pairs with every sequence moved one base later in its buffer,
+    so half of them start on the high nibble of a byte in the 4-bit layout."""
+    from paper_2301_09310_gb300.synth import Batch
+    return Batch(np.concatenate([np.full(1, 2, np.uint8), batch.q_seq]), batch.q_off + 1,
+                 batch.q_len, np.concatenate([np.full(1, 3, np.uint8), batch.t_seq]),
+                 batch.t_off + 1, batch.t_len, batch.h0)
+
+
+@pytest.mark.parametrize("odd", [0, 1])
+def test_packed4_reads(ctx, odd):
+    # two 4-bit codes per byte, unpacked on the GPU: batched, plain and
+    # BWA-compatible calls equal the oracle on the base codes
+    import torch
+    import oracle
+    import paper_2301_09310_gb300 as xt
+    from paper_2301_09310_gb300.synth import BwaScoringParams
+    wl = synth.WORKLOADS["c3_mixed"]
+    batches = [(synth.generate(wl, n=4000, first=777), wl.scoring),
+               (fuzz_batch(23, 600, max_len=80, tail=40), SCORINGS[3])]
+    other = xt.Context(0)
+    try:
+        other.set_alphabet(xt.XT_ALPHABET_PACKED4)
+        dev = torch.device("cuda", 0)
+        T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+        for batch, sc in batches:
+            if odd:
+                batch = _odd_start(batch)
+            want = run_oracle(batch, sc)
+            args = (T(xt.pack4(batch.q_seq)), T(batch.q_off), T(batch.q_len),
+                    T(xt.pack4(batch.t_seq)), T(batch.t_off), T(batch.t_len), T(batch.h0))
+            for plain in (False, True):
+                out, cells = other.extend(*args, sc, plain=plain)
+                torch.cuda.synchronize()
+                assert_same((out.cpu().numpy(), cells.cpu().numpy()), want,
+                            f"packed4 odd={odd} plain={plain}")
+            bsc = BwaScoringParams.from_scoring(sc)
+            out, cells = other.extend_bwa(*args, bsc)
+            torch.cuda.synchronize()
+            bwant = oracle.extend_batch_bwa(batch.q_seq, batch.q_off, batch.q_len, batch.t_seq,
+                                            batch.t_off, batch.t_len, batch.h0,
+                                            oracle.BwaScoring(*bsc.as_tuple()))
+            assert_same((out.cpu().numpy(), cells.cpu().numpy()), bwant, f"packed4 bwa odd={odd}")
+    finally:
+        other.close()
+
+
+def test_packed4_host_chunks_equal_codes():
+    # 2.1M pairs on host buffers: the call runs in chunks, copies packed
+    # bytes (half of the codes) and unpacks each chunk's bytes on the GPU;
+    # every result equals the same call on base codes
+    import paper_2301_09310_gb300 as xt
+    wl = synth.WORKLOADS["c2_short"]
+    b = synth.generate(wl, n=2_100_000)
+    sub = np.arange(0, b.n, 700)
+    want_sub = run_oracle(b.take(sub), wl.scoring)
+    res = {}
+    for alphabet in (xt.XT_ALPHABET_CODES, xt.XT_ALPHABET_PACKED4):
+        c = xt.Context(0)
+        try:
+            c.set_alphabet(alphabet)
+            q = b.q_seq if alphabet == xt.XT_ALPHABET_CODES else xt.pack4(b.q_seq)
+            t = b.t_seq if alphabet == xt.XT_ALPHABET_CODES else xt.pack4(b.t_seq)
+            res[alphabet] = c.extend_host(q, b.q_off, b.q_len, t, b.t_off, b.t_len, b.h0,
+                                          wl.scoring)
+        finally:
+            c.close()
+    (oc, cc), (op, cp) = res[xt.XT_ALPHABET_CODES], res[xt.XT_ALPHABET_PACKED4]
+    assert np.array_equal(oc, op) and np.array_equal(cc, cp)
+    assert_same((op[sub], cp[sub]), want_sub, "packed4 host chunks vs oracle")

@@ -129,3 +129,26 @@ def test_seeds_empty_and_bad_args(ctx):
         run_seeds(ctx, b, np.zeros(10, np.int32), np.zeros(10, np.int32),
                   np.full(10, 5, np.int32), np.full(10, 5, np.int32), ScoringParams(match=0))
     assert e.value.status == xt.XT_EINVAL
+
+
+def test_seeds_packed4_equal_codes(ctx):
+    # the 4-bit alphabet: both sides equal the call on base codes
+    import paper_2301_09310_gb300 as xt
+    wl = synth.WORKLOADS["c3_mixed"]
+    rng = np.random.default_rng(9)
+    b = synth.generate(wl, n=800, first=9000)
+    keep = (b.q_len >= 1) & (b.t_len >= 1)
+    b = b.take(np.nonzero(keep)[0])
+    seeds, q_beg, t_beg, seed_len = make_seeds(b, rng)
+    h0 = (seed_len * wl.scoring.match).astype(np.int32)
+    want = run_seeds(ctx, seeds, q_beg, t_beg, seed_len, h0, wl.scoring)
+    other = xt.Context(0)
+    try:
+        other.set_alphabet(xt.XT_ALPHABET_PACKED4)
+        packed = Batch(xt.pack4(seeds.q_seq), seeds.q_off, seeds.q_len, xt.pack4(seeds.t_seq),
+                       seeds.t_off, seeds.t_len, seeds.h0)
+        got = run_seeds(other, packed, q_beg, t_beg, seed_len, h0, wl.scoring)
+    finally:
+        other.close()
+    assert_same(got[0], want[0], "packed4 left")
+    assert_same(got[1], want[1], "packed4 right")
