@@ -345,6 +345,13 @@ constexpr int32_t kLaneSlots = 77824;    // one-lane thread slots of a full GPU 
 // finish fast even when a bucket leaves most lanes idle.
 constexpr int kLongJ = 10;               // buckets of queries longer than 510 bases
 inline int32_t lane_min_pairs(int j) { return j >= kLongJ ? 32768 : (j >= 7 ? kBucketSmall : 0); }
+// The longest query of bucket j, and the in-band cells of a pair of query
+// length q whose target runs to the band's end (q + w rows of at most 2w+1
+// columns): the planning estimates of a pair's work.
+inline double pair_cells_q(int j) { return (double)(((int64_t)1 << j) - 2); }
+inline double band_cells_est(double q, int w) {
+  return (q + (double)w) * std::min(q, 2.0 * (double)w + 1.0);
+}
 
 // Flags for classify: kJHuge where the default group ring does not fit
 // (band geometry only), kJPacked where a one-lane schedule is possible for
@@ -407,6 +414,15 @@ void plan_counts(xt_ctx* ctx, const Score& sc, const int32_t (*cnt)[kNumJ], cons
                  const bool* lane_ok, Plan* pl) {
   pl->jf = jf;
   const bool saved = ctx->plan_small;
+  // the call's estimated cells: each bucket's pairs at a query length three
+  // quarters of the way up the bucket
+  double est_cells = 0.0;
+  for (int cls = CLS_PACKED; cls < kNumClasses; ++cls)
+    for (int j = 0; j < kNumJ; ++j)
+      if (cnt[cls][j]) {
+        const int jj = j < kJMin ? kJMin : j;
+        est_cells += (double)cnt[cls][j] * band_cells_est(0.75 * pair_cells_q(jj), sc.w);
+      }
   // long queries: one lane per pair needs many pairs to fill the GPU, but
   // the long buckets of one call run side by side, so when together they
   // hold two full waves of lanes each of them takes the one-lane engine
@@ -442,9 +458,15 @@ void plan_counts(xt_ctx* ctx, const Score& sc, const int32_t (*cnt)[kNumJ], cons
         bool huge = false;
         const BucketSched* t = ctx->forced_P ? nullptr : tuned(ctx, sc.w, jj);
         if (!ctx->forced_P && !t && c < min_pairs(jj) && cls != CLS_WIDE) {
-          // enough lanes per pair to fill the GPU, where the ring fits
-          int want = 4;
-          while (want < 32 && (int64_t)want * c < kLaneSlots) want *= 2;
+          // enough lanes per pair that the bucket's longest pair takes no
+          // longer than the call's whole work spread over the GPU's one-lane
+          // slots (the call's buckets run side by side, so a small bucket
+          // need not fill the GPU on its own; fewer lanes per pair waste less
+          // of each chunk on the wavefront's fill), where the ring fits
+          const double need = band_cells_est(pair_cells_q(jj), sc.w) * (double)kLaneSlots /
+                              std::max(est_cells, 1.0);
+          int want = 4;  // two-lane groups measured slower than four on every call size
+          while (want < 32 && want < need) want *= 2;
           for (int q = want; q >= 2 && P == 0; q /= 2) {
             const int l = queue_ring_log2(jj, sc.w, q, 8);
             if (l <= kQueueRsCapLog2 && queue_smem_bytes(q, l) <= (size_t)ctx->smem_optin / 2 - 1024) {
