@@ -448,7 +448,15 @@ void plan_counts(xt_ctx* ctx, const Score& sc, const int32_t (*cnt)[kNumJ], cons
         } else if (!ctx->forced_P) {
           const BucketSched* t = tuned(ctx, sc.w, jj);
           if (t) lane = t->P == 1;
-          else if (c < min_pairs(jj)) lane = false;  // latency rule below
+          // latency rule below; a long bucket still takes one lane per pair
+          // when its longest pair on one lane takes at most half of the call's
+          // whole work spread over the GPU (the one-lane engine is the
+          // cheapest per cell, and the call's other buckets fill the slots it
+          // leaves; without the factor two, 400k- and 1M-pair calls of the
+          // c5 mix measured slower)
+          else if (c < min_pairs(jj))
+            lane = jj >= kLongJ && 2.0 * band_cells_est(pair_cells_q(jj), sc.w) *
+                                           (double)kLaneSlots <= est_cells;
         }
       }
       if (lane) {
