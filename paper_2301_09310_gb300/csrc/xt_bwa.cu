@@ -375,8 +375,21 @@ __device__ __forceinline__ void score_row(uint32_t ti, uint32_t mism4, uint32_t 
 // boundary: column beg-1 (x = H of column -1 for the next row: the deletion
 // run from the seed, else 0) and column end (y = its query code << 28 | 0).
 // F and H stay below 2^28: H <= h0 + qlen * match <= 2^20 + 2^20 * 127.
-template <int G, int K>
-__device__ __forceinline__ void bwa_pair(const BwaArgs& a, const Group<G>& g, int2* buf,
+// A group's row buffer, element e at base[e * S]: the buffers of the S groups
+// that share a half-warp are interleaved element by element (S = 16 / G for
+// groups of up to 8 lanes, else 1).  With each lane's columns an odd count,
+// the G lanes of a group then fall on distinct bank pairs of one residue
+// class mod 2S, and the S groups on different classes, so a half-warp's
+// 8-byte accesses meet no bank conflict whatever each group's row offsets.
+template <int S>
+struct RowBuf {
+  int2* base;
+  __device__ __forceinline__ int2& operator[](int32_t e) const { return base[e * S]; }
+  __device__ __forceinline__ RowBuf operator+(int32_t e) const { return RowBuf{base + e * S}; }
+};
+
+template <int G, int K, typename Buf>
+__device__ __forceinline__ void bwa_pair(const BwaArgs& a, const Group<G>& g, Buf buf,
                                          int32_t k) {
   const BwaScore& sc = a.sc;
   const int32_t qlen = a.q_len[k], tlen = a.t_len[k], h0 = a.h0[k];
@@ -432,11 +445,11 @@ __device__ __forceinline__ void bwa_pair(const BwaArgs& a, const Group<G>& g, in
     // first column's word waits for the barrier when the origin moved: the
     // lane before reads column first-1's y word in this pass.
     const bool moved = o_row != o_up;
-    int2* wr = buf + (first - o_row);
+    const Buf wr = buf + (first - o_row);
     int32_t Hp[K];
     int32_t Y = 0, y_first = 0;
     if (cnt > 0) {
-      const int2* rd = buf + (first - 1 - o_up);
+      const Buf rd = buf + (first - 1 - o_up);
       int32_t Dn = rd[0].x;
 #pragma unroll
       for (int kk = 0; kk < K; ++kk) {
@@ -545,7 +558,11 @@ __global__ void __launch_bounds__(kBwaWarpThreads, 6) k_bwa_seg(BwaArgs a, int32
   __shared__ int2 s_buf[Cl::kPairsPerBlock * Cl::kBufElems];
   Group<G> g;
   g.init();
-  int2* buf = s_buf + (threadIdx.x / G) * Cl::kBufElems;
+  // the S groups of a half-warp interleave their buffers (see RowBuf)
+  constexpr int S = G <= 8 ? 16 / G : 1;
+  static_assert(Cl::kPairsPerBlock % S == 0, "groups of a block fill whole interleaved sets");
+  const int gi = threadIdx.x / G;
+  const RowBuf<S> buf{s_buf + (gi / S) * S * Cl::kBufElems + gi % S};
   for (;;) {
     const int32_t p = g.claim(&a.heads[C]);
     if (p >= count) break;
@@ -574,7 +591,7 @@ __global__ void __launch_bounds__(BwaClass<C>::G, 512 / BwaClass<C>::G)
     if (idx < 0 || idx >= a.n) break;
     const int32_t k = a.order[idx];
     if (k < 0 || k >= a.n) continue;
-    bwa_pair<G, Cl::K>(a, g, d_buf, k);
+    bwa_pair<G, Cl::K>(a, g, RowBuf<1>{d_buf}, k);
   }
 }
 
