@@ -256,7 +256,7 @@ def measure_int_rates(local):
             "ms": {k: round(ms, 4) for k, (_, ms) in raw.items()},
             "sm_mhz": mhz, "sms": sms, "clocks": clocks,
             "alu_pipe": max(per_clk[k] for k in ALU_PROBES),
-            "mad_pipe": per_clk["imad.u32"], "issue": per_clk["max.s16x2 + add.s16x2 interleaved"],
+            "mad_pipe": per_clk["imad.u32"], "issue": per_clk["max3.s16x2 + add.s16x2 by chain"],
             "cell_update_cells": per_clk["packed cell update (cells)"]}
 
 
@@ -287,7 +287,7 @@ def int_roofline(updates, kernel_ms, rates, mhz, alu_ops=ALU_OPS_PER_UPDATE,
             "issue": {"achieved": round(all_ach, 3), "peak": round(issue_peak, 3),
                       "frac": round(all_ach / issue_peak, 4),
                       "basis": f"measured issue probe {rates['issue']:.2f} thread-instr/SM/clk "
-                               "(ALU and multiply-add pipes interleaved), every algorithmic "
+                               "(ALU and multiply-add pipes, half the chains each), every algorithmic "
                                "instruction counted, of measured"},
             "cell_update_ceiling": {
                 "updates_per_s": round(rates["cell_update_cells"] / 2 * clk, 1),

@@ -424,10 +424,9 @@ xt_status xt_shard_lpt(const int32_t* q_len, const int32_t* t_len, int32_t n_pai
  * instruction in independent chains on every SM (8 chains per thread, a full
  * SM of warps) and is timed with CUDA events after one warm-up launch; the
  * best of `reps` launches is returned: *units instructions (thread-level) in
- * *ms milliseconds.  XT_RATE_MIX interleaves a packed max (integer ALU
- * pipe) and a packed add (multiply-add pipe) in every chain, two-source
- * instructions of the two pipes, so it measures the issue rate (*units
- * counts both).  XT_RATE_CELL_P16 runs the packed cell update of
+ * *ms milliseconds.  XT_RATE_MIX runs the 3-way packed max (integer ALU
+ * pipe) in half of the chains and the packed add (multiply-add pipe) in the
+ * other half, so both pipes feed the issue slots: it measures the issue rate.  XT_RATE_CELL_P16 runs the packed cell update of
  * the one-lane engine on registers (the engine's fast step, 16 cells per step
  * and thread); *units then counts cells.  Synchronous; allocates a few bytes
  * of device memory; XT_EINVAL for an unknown op or device.
@@ -439,8 +438,9 @@ xt_status xt_shard_lpt(const int32_t* q_len, const int32_t* t_len, int32_t n_pai
 #define XT_RATE_IADD3 4        /* 32-bit three-input add */
 #define XT_RATE_MAX3_32 5      /* 3-way 32-bit max */
 #define XT_RATE_IMAD 6         /* 32-bit multiply-add */
-#define XT_RATE_MIX 7          /* packed max and packed add, interleaved */
+#define XT_RATE_MIX 7          /* 3-way packed max and packed add, by chain */
 #define XT_RATE_CELL_P16 8     /* the packed cell update (cells, not instructions) */
+#define XT_RATE_HMAX2 9        /* packed half-precision max */
 xt_status xt_int_rate(int device, int op, int reps, int64_t* units, double* ms);
 
 /* Human-readable name of a status code (static storage). */

@@ -36,11 +36,13 @@ XT_STATIC_MAX_PAIRS = 1 << 20
 # instruction kinds of xt_int_rate (measurement aid)
 XT_RATE_ADD16X2, XT_RATE_MAX3_16X2, XT_RATE_ADDMAX_16X2, XT_RATE_PRMT = 0, 1, 2, 3
 XT_RATE_IADD3, XT_RATE_MAX3_32, XT_RATE_IMAD, XT_RATE_MIX, XT_RATE_CELL_P16 = 4, 5, 6, 7, 8
+XT_RATE_HMAX2 = 9
 RATE_NAMES = {XT_RATE_ADD16X2: "add.s16x2", XT_RATE_MAX3_16X2: "max3.s16x2",
               XT_RATE_ADDMAX_16X2: "addmax.relu.s16x2", XT_RATE_PRMT: "prmt",
               XT_RATE_IADD3: "iadd3.s32", XT_RATE_MAX3_32: "max3.s32", XT_RATE_IMAD: "imad.u32",
-              XT_RATE_MIX: "max.s16x2 + add.s16x2 interleaved",
-              XT_RATE_CELL_P16: "packed cell update (cells)"}
+              XT_RATE_MIX: "max3.s16x2 + add.s16x2 by chain",
+              XT_RATE_CELL_P16: "packed cell update (cells)",
+              XT_RATE_HMAX2: "max.f16x2"}
 
 
 class xt_scoring(ctypes.Structure):
