@@ -53,6 +53,7 @@ struct Launch {
   int64_t slab = 0;          // entries per global slab (power of two)
   int grid = 0;              // CTAs
   int mparam = 0;            // one-lane engine: match + 1 (32-bit) or shift k (packed)
+  size_t pool_off = 0;       // global ring: byte offset of the launch's slabs in the pool
 };
 
 // Host-side launchers (defined in xt_kernels.cu); all enqueue on `stream`.
