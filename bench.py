@@ -99,8 +99,10 @@ def parse_args():
     ap.add_argument("--schedule", default="",
                     help="P,R: one forced schedule for every bucket (profiling a kernel on a "
                          "subset of a workload); default: the count-aware plan")
-    ap.add_argument("--serve-slots", type=int, default=3)
-    ap.add_argument("--serve-batch-mib", type=int, default=256,
+    ap.add_argument("--serve-slots", type=int, default=2)
+    ap.add_argument("--serve-batch-pairs", type=int, default=0,
+                    help="pairs per batch at most (0: library default)")
+    ap.add_argument("--serve-batch-mib", type=int, default=1024,
                     help="staged bytes per batch (the slot capacity), MiB")
     ap.add_argument("--serve-budget-gb", type=float, default=40.0,
                     help="device memory budget of the whole server, GB")
@@ -914,7 +916,9 @@ def serve_leg(args, local, stream):
                         "sigma 1 clipped [1,2000], tlen = qlen + 200; requests U[1,4096] "
                         "pairs, Poisson arrivals",
             "api": f"xt_serve_submit/xt_serve_wait (host buffers; {args.serve_slots} slots of "
-                   f"{args.serve_batch_mib} MiB, device budget {args.serve_budget_gb:g} GB, "
+                   f"{args.serve_batch_mib} MiB and "
+                   f"{args.serve_batch_pairs or 'the default'} pairs at most, "
+                   f"device budget {args.serve_budget_gb:g} GB, "
                    f"gather threads {args.serve_gather_threads or 'default'})",
             "latency": "scheduled arrival -> results in host memory",
             "schedules": "levels: built-in count-aware schedules (the server's default); "
@@ -954,7 +958,8 @@ def serve_levels(args, local, b, wl, peak_pairs, ref_out, ref_cells, total_cells
                           ctypes.c_void_p(out.ctypes.data + 28 * a),
                           ctypes.c_void_p(cells.ctypes.data + 8 * a)))
         srv = xt.xt_serve_create(local, xt.xt_serve_config(
-            args.serve_slots, 0, args.serve_batch_mib << 20, 0, int(args.serve_budget_gb * 1e9),
+            args.serve_slots, args.serve_batch_pairs, args.serve_batch_mib << 20, 0,
+            int(args.serve_budget_gb * 1e9),
             args.serve_gather_threads, table.encode() if table else None, 0))
         tickets = queue.Queue()
         stamps = np.zeros((nreq, 4), np.int64)   # arrival, submit, launch, done

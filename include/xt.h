@@ -516,10 +516,10 @@ xt_status xt_extend_batch_static(const uint8_t* q_seq, int64_t q_bytes, const in
 typedef struct xt_server xt_server;
 
 typedef struct {
-  int32_t slots;            /* batches in flight at once, 1..8 (0: 3) */
+  int32_t slots;            /* batches in flight at once, 1..8 (0: 2) */
   int32_t max_batch_pairs;  /* pairs per batch, <= 1 << 24 (0: 1 << 20) */
   int64_t max_batch_bytes;  /* staged input bytes per batch: sequences plus
-                               28 bytes per pair (0: 256 MiB) */
+                               28 bytes per pair (0: 1 GiB) */
   int64_t max_queued_bytes; /* staged bytes of waiting requests (0: 1 GiB) */
   size_t mem_budget_bytes;  /* device memory of the whole server (0: no cap) */
   int32_t gather_threads;   /* host threads staging a batch, 1..16, the server

@@ -426,9 +426,11 @@ xt_status xt_serve_create(xt_server** out, int device, const xt_serve_config* cf
   *out = nullptr;
   xt_serve_config cfg{};
   if (cfg_in) cfg = *cfg_in;
-  if (cfg.slots == 0) cfg.slots = 3;
+  // defaults: two slots of 1 GiB (c5 stream at 90% of the batched peak: 43.2-43.8M pairs/s,
+  // p99 57-62 ms, against 38.4M and 84 ms with three slots of 256 MiB)
+  if (cfg.slots == 0) cfg.slots = 2;
   if (cfg.max_batch_pairs == 0) cfg.max_batch_pairs = 1 << 20;
-  if (cfg.max_batch_bytes == 0) cfg.max_batch_bytes = (int64_t)256 << 20;
+  if (cfg.max_batch_bytes == 0) cfg.max_batch_bytes = (int64_t)1 << 30;
   if (cfg.max_queued_bytes == 0) cfg.max_queued_bytes = (int64_t)1 << 30;
   if (cfg.gather_threads == 0) {
     const int hw = (int)std::thread::hardware_concurrency();
