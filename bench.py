@@ -1010,10 +1010,24 @@ def serve_levels(args, local, b, wl, peak_pairs, ref_out, ref_cells, total_cells
             raise RuntimeError(f"served requests failed: {set(status)}")
         lat = (stamps[:, 3] - stamps[:, 0]) / 1e6
         span = (stamps[:, 3].max() - t0) / 1e9
+        # steady state: the pairs whose results landed in the last three
+        # quarters of the arrival window, per second of that window (a server
+        # that keeps up completes pairs as fast as they arrive; the drain after
+        # the last arrival, one batch latency, is left out)
+        t_arr = int(arrive.max())
+        w0 = t0 + (t_arr - t0) // 4
+        done_in = (stamps[:, 3] >= w0) & (stamps[:, 3] <= t_arr)
+        steady = float(rs.size[done_in].sum()) / ((t_arr - w0) / 1e9)
+        half = stamps[:, 0] < t0 + (t_arr - t0) // 2
         levels.append({
             "offered_frac_of_peak": frac,
             "offered_pairs_per_s": round(frac * peak_pairs, 1),
             "achieved_pairs_per_s": round(b.n / span, 1),
+            "steady_pairs_per_s": round(steady, 1),
+            "arrival_ms": round((t_arr - t0) / 1e6, 3),
+            "drain_ms": round((stamps[:, 3].max() - t_arr) / 1e6, 3),
+            "p99_ms_first_half": round(float(np.percentile(lat[half], 99)), 3),
+            "p99_ms_second_half": round(float(np.percentile(lat[~half], 99)), 3),
             "gcups": round(total_cells / span / 1e9, 3),
             "p50_ms": round(float(np.percentile(lat, 50)), 3),
             "p99_ms": round(float(np.percentile(lat, 99)), 3),

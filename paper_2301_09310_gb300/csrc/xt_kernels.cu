@@ -35,12 +35,23 @@ __device__ __forceinline__ void bucket_of(int32_t ql, int* j_out, int* sub_out) 
 // ---------------------------------------------------------------- classify
 // Validates every pair, writes the results of invalid and degenerate pairs
 // directly, and assigns the others a class and a (bucket, sub-bucket) by
-// query length, counted for the ordering pass.
-__global__ void k_classify(const Batch* __restrict__ bd, Score sc, int32_t match, int32_t mshift,
-                           JFlags jfl, Work w) {
-  const Batch b = *bd;
-  const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= b.n) return;
+// query length, counted for the ordering pass.  A block takes kOrdPer x
+// kOrdThreads consecutive pairs and counts them in a shared-memory histogram
+// of every (class, bucket, sub-bucket), then adds its non-zero bins to the
+// global counts: a batch's pairs fall into a few hundred bins, and one global
+// atomic per pair on those bins serialised the pass.
+constexpr int kOrdThreads = 1024;
+constexpr int kOrdPer = 8;
+constexpr int kOrdPairs = kOrdThreads * kOrdPer;  // pairs per block
+
+__device__ __forceinline__ void hist_clear(int32_t* s_hist) {
+  for (int i = threadIdx.x; i < kNumBuckets; i += kOrdThreads) s_hist[i] = 0;
+}
+
+// Class of pair k (CLS_DONE after writing the result of an invalid or
+// degenerate pair) and its histogram bin.
+__device__ __forceinline__ int classify_pair(const Batch& b, int32_t k, int32_t match,
+                                             int32_t mshift, const uint8_t* s_jf, int* bin) {
   const int64_t qo = b.q_off[k], to = b.t_off[k];
   const int32_t ql = b.q_len[k], tl = b.t_len[k], h0 = b.h0[k];
   const bool ok = h0 >= 1 && h0 <= XT_MAX_H0 && ql >= 0 && tl >= 0 && ql <= XT_MAX_LEN &&
@@ -48,31 +59,58 @@ __global__ void k_classify(const Batch* __restrict__ bd, Score sc, int32_t match
                   to <= b.t_bytes - tl;
   if (!ok) {
     write_result(b, k, 0, 0, 0, 0, 0, 0, XT_EINVAL, 0);
-    w.pclass[k] = CLS_DONE;
-    return;
+    return CLS_DONE;
   }
   if (ql == 0) {
     write_result(b, k, h0, 0, 0, h0, 0, 0, XT_OK, 0);
-    w.pclass[k] = CLS_DONE;
-    return;
+    return CLS_DONE;
   }
   if (tl == 0) {
     write_result(b, k, h0, 0, 0, -1, 0, 0, XT_OK, 0);
-    w.pclass[k] = CLS_DONE;
-    return;
+    return CLS_DONE;
   }
   int j, sub;
   bucket_of(ql, &j, &sub);
   const int64_t bound = (int64_t)h0 + (int64_t)match * (ql < tl ? ql : tl);
   const bool wide = bound > 32767 || ql > 65535;
-  const uint8_t jf = jfl.f[j];
+  const uint8_t jf = s_jf[j];
   int cls = wide ? CLS_WIDE : CLS_NARROW;
   // packed: the anchoring multiply and the 16-bit row keys (H * 64 + step) fit
   if (!wide && (jf & kJPacked) && ((bound + 1) << mshift) <= 32767 && bound * 64 + 63 <= 32767)
     cls = CLS_PACKED;
   if ((jf & kJHuge) || (cls == CLS_WIDE && (jf & kJHugeWide))) cls = CLS_HUGE;
-  w.pclass[k] = (uint8_t)cls;
-  atomicAdd(&w.counts[(cls * kNumJ + j) * kNumSub + sub], 1);
+  *bin = (cls * kNumJ + j) * kNumSub + sub;
+  return cls;
+}
+
+__global__ void __launch_bounds__(kOrdThreads) k_classify(const Batch* __restrict__ bd, Score sc,
+                                                          int32_t match, int32_t mshift,
+                                                          JFlags jfl, Work w) {
+  extern __shared__ int32_t s_hist[];  // [kNumBuckets]
+  // the bucket flags, indexed by a runtime bucket: shared memory, not a
+  // local copy of the by-value argument
+  __shared__ uint8_t s_jf[kNumJ];
+  if (threadIdx.x < kNumJ) s_jf[threadIdx.x] = jfl.f[threadIdx.x];
+  const Batch b = *bd;
+  hist_clear(s_hist);
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kOrdPairs;
+#pragma unroll 1
+  for (int r = 0; r < kOrdPer; ++r) {
+    const int64_t kk = base + r * kOrdThreads + threadIdx.x;
+    if (kk < b.n) {
+      const int32_t k = (int32_t)kk;
+      int bin = 0;
+      const int cls = classify_pair(b, k, match, mshift, s_jf, &bin);
+      w.pclass[k] = (uint8_t)cls;
+      if (cls < kNumClasses) atomicAdd(&s_hist[bin], 1);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kNumBuckets; i += kOrdThreads) {
+    const int32_t c = s_hist[i];
+    if (c) atomicAdd(&w.counts[i], c);
+  }
 }
 
 // Exclusive scan of the bucket counts in queue order: per class, buckets from
@@ -137,17 +175,41 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(Work w) {
   }
 }
 
-__global__ void k_scatter(const Batch* __restrict__ bd, Work w) {
-  const Batch b = *bd;
-  const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= b.n) return;
-  const int cls = w.pclass[k];
-  if (cls >= kNumClasses) return;
-  const int32_t ql = b.q_len[k];
-  int j, sub;
-  bucket_of(ql, &j, &sub);
-  const int32_t pos = atomicAdd(&w.cursor[(cls * kNumJ + j) * kNumSub + sub], 1);
-  w.order[pos] = k;
+// Each block ranks its pairs within their bins in shared memory, reserves one
+// run of queue slots per non-zero bin with one global atomic (the scan left
+// every bin's cursor at its first slot) and writes the pairs' indices there.
+__global__ void __launch_bounds__(kOrdThreads) k_scatter(const Batch* __restrict__ bd, Work w) {
+  extern __shared__ int32_t s_hist[];  // [kNumBuckets]: counts, then run starts
+  const int32_t n = bd->n;
+  const int32_t* __restrict__ q_len = bd->q_len;
+  hist_clear(s_hist);
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kOrdPairs;
+  int bin[kOrdPer], rank[kOrdPer];
+#pragma unroll
+  for (int r = 0; r < kOrdPer; ++r) {
+    const int64_t kk = base + r * kOrdThreads + threadIdx.x;
+    bin[r] = -1;
+    rank[r] = 0;
+    if (kk < n) {
+      const int cls = w.pclass[kk];
+      if (cls < kNumClasses) {
+        int j, sub;
+        bucket_of(q_len[kk], &j, &sub);
+        bin[r] = (cls * kNumJ + j) * kNumSub + sub;
+        rank[r] = atomicAdd(&s_hist[bin[r]], 1);
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kNumBuckets; i += kOrdThreads) {
+    const int32_t c = s_hist[i];
+    if (c) s_hist[i] = atomicAdd(&w.cursor[i], c);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kOrdPer; ++r)
+    if (bin[r] >= 0) w.order[s_hist[bin[r]] + rank[r]] = (int32_t)(base + r * kOrdThreads + threadIdx.x);
 }
 
 __device__ __forceinline__ Pair load_pair(const Batch& b, int32_t k) {
@@ -592,21 +654,27 @@ cudaError_t raise_smem_limit(K kern, size_t smem) {
   return e;
 }
 
+constexpr size_t kHistBytes = sizeof(int32_t) * (size_t)kNumBuckets;
+
 cudaError_t launch_classify(const Batch* bd, int32_t n_cap, const Score& sc, int32_t match,
                             const JFlags& jf, const Work& w, cudaStream_t stream) {
   if (n_cap == 0) return cudaSuccess;
-  const int T = 256;
   int mshift = 0;
   while ((1 << mshift) < match + 1) ++mshift;
-  k_classify<<<(n_cap + T - 1) / T, T, 0, stream>>>(bd, sc, match, mshift, jf, w);
+  cudaError_t e = raise_smem_limit(k_classify, kHistBytes);
+  if (e != cudaSuccess) return e;
+  const int grid = (int)(((int64_t)n_cap + kOrdPairs - 1) / kOrdPairs);
+  k_classify<<<grid, kOrdThreads, kHistBytes, stream>>>(bd, sc, match, mshift, jf, w);
   return cudaGetLastError();
 }
 
 cudaError_t launch_order(const Batch* bd, int32_t n_cap, const Work& w, cudaStream_t stream) {
   k_scan<<<1, kScanThreads, 0, stream>>>(w);
   if (n_cap > 0) {
-    const int T = 256;
-    k_scatter<<<(n_cap + T - 1) / T, T, 0, stream>>>(bd, w);
+    cudaError_t e = raise_smem_limit(k_scatter, kHistBytes);
+    if (e != cudaSuccess) return e;
+    const int grid = (int)(((int64_t)n_cap + kOrdPairs - 1) / kOrdPairs);
+    k_scatter<<<grid, kOrdThreads, kHistBytes, stream>>>(bd, w);
   }
   return cudaGetLastError();
 }
