@@ -77,14 +77,20 @@ static_assert(2 * (4 * kNumClasses * kNumJ + 255) / 4 <= kSegHostSeedTotals, "bu
 static_assert(kSegHostSeedTotals + 4 <= kSegHostBwaCounts, "seed totals");
 static_assert(kSegHostBwaCounts + 16 <= kSegHostChunkEnds, "BWA class sizes");
 static_assert(kSegHostChunkEnds + 4 * kMaxChunks <= kSegHostWords, "chunk ends");
-constexpr int32_t kChunkPairs = 1 << 20;   // pairs per chunk at least (a chunk fills the GPU)
+constexpr int32_t kChunkPairs = 1 << 20;   // calls of 2 x this many pairs or more are chunked
+constexpr int32_t kChunkFirstMin = 1 << 18; // pairs in the first (smallest) chunk at least
+// First pair of each chunk of a host-buffer call (multiples of 256).
+struct ChunkStarts {
+  int32_t start[kMaxChunks];
+  int32_t count;
+};
 // ends[2k], ends[2k+1]: how far chunk k's pairs read into the query and the
 // target buffer (see xt_stage.cu); ends must be zeroed first.
 // Store a call's batch descriptor into device memory (one thread; the
 // descriptor travels as a kernel parameter).
 cudaError_t launch_store_desc(Batch* dst, const Batch& b, cudaStream_t stream);
 cudaError_t launch_chunk_ends(const int64_t* q_off, const int32_t* q_len, const int64_t* t_off,
-                              const int32_t* t_len, int32_t n, int32_t chunk_pairs,
+                              const int32_t* t_len, int32_t n, const ChunkStarts& cb,
                               int64_t q_bytes, int64_t t_bytes, unsigned long long* ends,
                               cudaStream_t stream);
 

@@ -12,13 +12,13 @@ namespace {
 constexpr int kStageThreads = 256;
 
 // ends[2k] / ends[2k+1]: the largest q_off + q_len / t_off + t_len over the
-// pairs of chunk k (pairs [k * chunk_pairs, (k+1) * chunk_pairs)), clamped to
-// [0, q_bytes] / [0, t_bytes].  chunk_pairs is a multiple of the block size,
+// pairs of chunk k (pairs [cb.start[k], cb.start[k+1])), clamped to
+// [0, q_bytes] / [0, t_bytes].  Chunk starts are multiples of the block size,
 // so a block never spans two chunks; ends must start at 0.
 __global__ void __launch_bounds__(kStageThreads)
 k_chunk_ends(const int64_t* __restrict__ q_off, const int32_t* __restrict__ q_len,
              const int64_t* __restrict__ t_off, const int32_t* __restrict__ t_len, int32_t n,
-             int32_t chunk_pairs, int64_t q_bytes, int64_t t_bytes,
+             ChunkStarts cb, int64_t q_bytes, int64_t t_bytes,
              unsigned long long* __restrict__ ends) {
   __shared__ unsigned long long s_q[kStageThreads / 32], s_t[kStageThreads / 32];
   const int64_t p = (int64_t)blockIdx.x * kStageThreads + threadIdx.x;
@@ -51,7 +51,8 @@ k_chunk_ends(const int64_t* __restrict__ q_off, const int32_t* __restrict__ q_le
     }
     const int64_t base = (int64_t)blockIdx.x * kStageThreads;
     if (base < n) {
-      const int k = (int)(base / chunk_pairs);
+      int k = 0;
+      while (k + 1 < cb.count && base >= cb.start[k + 1]) ++k;
       atomicMax(&ends[2 * k], qe);
       atomicMax(&ends[2 * k + 1], te);
     }
@@ -68,13 +69,16 @@ cudaError_t launch_store_desc(Batch* dst, const Batch& b, cudaStream_t stream) {
 }
 
 cudaError_t launch_chunk_ends(const int64_t* q_off, const int32_t* q_len, const int64_t* t_off,
-                              const int32_t* t_len, int32_t n, int32_t chunk_pairs, int64_t q_bytes,
-                              int64_t t_bytes, unsigned long long* ends, cudaStream_t stream) {
+                              const int32_t* t_len, int32_t n, const ChunkStarts& cb,
+                              int64_t q_bytes, int64_t t_bytes, unsigned long long* ends,
+                              cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
-  if (chunk_pairs <= 0 || chunk_pairs % kStageThreads != 0) return cudaErrorInvalidValue;
+  if (cb.count < 1 || cb.count > kMaxChunks || cb.start[0] != 0) return cudaErrorInvalidValue;
+  for (int k = 1; k < cb.count; ++k)
+    if (cb.start[k] % kStageThreads != 0 || cb.start[k] <= cb.start[k - 1]) return cudaErrorInvalidValue;
   const int grid = (int)(((int64_t)n + kStageThreads - 1) / kStageThreads);
-  k_chunk_ends<<<grid, kStageThreads, 0, stream>>>(q_off, q_len, t_off, t_len, n, chunk_pairs,
-                                                    q_bytes, t_bytes, ends);
+  k_chunk_ends<<<grid, kStageThreads, 0, stream>>>(q_off, q_len, t_off, t_len, n, cb, q_bytes,
+                                                    t_bytes, ends);
   return cudaGetLastError();
 }
 
