@@ -191,6 +191,11 @@ xt_status xt_extend_batch_plain(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_byt
  * meaning, every pointer a host pointer; pinned memory is fastest).  Copies
  * the inputs to the device, extends, copies results (and cells when
  * cells_out != NULL) back, and returns after the stream has synchronised.
+ * From 2 x 2^20 pairs the call runs in chunks of doubling size whose bytes
+ * copy while earlier chunks extend; a context created without a memory
+ * budget runs them on two internal contexts of its own (created on the
+ * first such call, released with the context), so that a chunk's kernels
+ * overlap the previous chunk's.
  */
 xt_status xt_extend_batch_host(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_bytes,
                                const int64_t* q_off, const int32_t* q_len, const uint8_t* t_seq,

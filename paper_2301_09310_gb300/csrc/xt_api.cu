@@ -916,6 +916,11 @@ xt_status xt_ctx_create(xt_ctx** out, int device, size_t mem_budget_bytes) {
 
 xt_status xt_ctx_destroy(xt_ctx* ctx) {
   if (!ctx) return XT_EINVAL;
+  for (auto*& c : ctx->chunk_ctx)
+    if (c) {
+      xt_ctx_destroy(c);
+      c = nullptr;
+    }
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
   if (ctx->work) cudaFree(ctx->work);
@@ -1115,6 +1120,31 @@ xt_status seeds_codes(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_bytes, const 
 
 extern "C" {
 
+namespace {
+
+// The two chunk contexts of ctx, created on first use, with ctx's schedule
+// settings; they read base codes.
+xt_status chunk_contexts(xt_ctx* ctx) {
+  for (auto*& c : ctx->chunk_ctx) {
+    if (!c) {
+      xt_status s = xt_ctx_create(&c, ctx->device, 0);
+      if (s != XT_OK) {
+        c = nullptr;
+        return fail(ctx, s, "chunk context");
+      }
+    }
+    c->tuning = ctx->tuning;
+    c->forced_P = ctx->forced_P;
+    c->forced_R = ctx->forced_R;
+    c->branches = ctx->branches;
+    c->graphs = ctx->graphs;
+    c->alphabet = XT_ALPHABET_CODES;
+  }
+  return XT_OK;
+}
+
+}  // namespace
+
 xt_status xt_extend_batch_host(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_bytes,
                                const int64_t* q_off, const int32_t* q_len, const uint8_t* t_seq,
                                int64_t t_bytes, const int64_t* t_off, const int32_t* t_len,
@@ -1249,23 +1279,59 @@ xt_status xt_extend_batch_host(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_byte
   // the chunks read the unpacked codes (the context's alphabet is codes for them)
   const uint8_t* cq = (const uint8_t*)(d + (packed ? o_qc : o_q));
   const uint8_t* ct = (const uint8_t*)(d + (packed ? o_tc : o_t));
+  // Without a memory budget the chunks alternate between two contexts of
+  // their own (workspace, ring pool, streams): chunk k classifies as soon as
+  // the metadata is on the device, and its extension kernels wait only for
+  // its own bytes, so they take the slots that chunk k-1's kernels leave as
+  // they drain.  Chunk k+2 reuses chunk k's context after it in stream order.
+  const bool apart = ctx->budget == 0 && !ctx->timing;
+  if (apart) {
+    s = chunk_contexts(ctx);
+    if (s != XT_OK) {
+      cudaStreamSynchronize(cs);
+      cudaStreamSynchronize(st);
+      return s;
+    }
+  }
+  auto sync_all = [&]() {
+    cudaStreamSynchronize(cs);
+    cudaStreamSynchronize(st);
+    if (apart)
+      for (auto* c : ctx->chunk_ctx) cudaStreamSynchronize(c->copy_stream);
+  };
   const int alphabet = ctx->alphabet;
   ctx->alphabet = XT_ALPHABET_CODES;
   for (int k = 0; k < chunks; ++k) {
     const int32_t p0 = cb.start[k];
     const int32_t p1 = k + 1 < chunks ? cb.start[k + 1] : n_pairs;
     if (p1 <= p0) continue;
-    e = cudaStreamWaitEvent(st, ev[2 + k], 0);
-    if (e != cudaSuccess) break;
-    s = run(ctx, false, cq, qn, dqo + p0, dql + p0, ct, tn, dto + p0, dtl + p0, dh0 + p0, p1 - p0,
-            sc, dout + p0, dcells ? dcells + p0 : nullptr, st);
+    xt_ctx* cc = apart ? ctx->chunk_ctx[k & 1] : ctx;
+    cudaStream_t cst = apart ? cc->copy_stream : st;
+    if (apart) {
+      e = cudaStreamWaitEvent(cst, ev[1], 0);
+      if (e != cudaSuccess) break;
+      s = run_begin(cc, false, cq, qn, dqo + p0, dql + p0, ct, tn, dto + p0, dtl + p0, dh0 + p0,
+                    p1 - p0, sc, dout + p0, dcells ? dcells + p0 : nullptr, cst);
+      if (s == XT_OK) {
+        e = cudaStreamWaitEvent(cst, ev[2 + k], 0);
+        s = e == cudaSuccess ? run_finish(cc) : cuda_fail(cc, e, "chunk bytes");
+      }
+      if (s != XT_OK) {
+        cc->pending.active = false;
+        ctx->last_error = cc->last_error;
+      }
+    } else {
+      e = cudaStreamWaitEvent(st, ev[2 + k], 0);
+      if (e != cudaSuccess) break;
+      s = run(ctx, false, cq, qn, dqo + p0, dql + p0, ct, tn, dto + p0, dtl + p0, dh0 + p0,
+              p1 - p0, sc, dout + p0, dcells ? dcells + p0 : nullptr, st);
+    }
     if (s != XT_OK) {
       ctx->alphabet = alphabet;
-      cudaStreamSynchronize(cs);
-      cudaStreamSynchronize(st);
+      sync_all();
       return s;
     }
-    e = cudaEventRecord(ev[2 + chunks + k], st);
+    e = cudaEventRecord(ev[2 + chunks + k], cst);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[2 + chunks + k], 0);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(out + p0, dout + p0, sizeof(xt_result) * (size_t)(p1 - p0),
@@ -1280,6 +1346,11 @@ xt_status xt_extend_batch_host(xt_ctx* ctx, const uint8_t* q_seq, int64_t q_byte
   if (e == cudaSuccess) e = e2;
   e2 = cudaStreamSynchronize(st);
   if (e == cudaSuccess) e = e2;
+  if (apart)
+    for (auto* c : ctx->chunk_ctx) {
+      e2 = cudaStreamSynchronize(c->copy_stream);
+      if (e == cudaSuccess) e = e2;
+    }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "chunked host call");
   return XT_OK;
 }
@@ -1376,6 +1447,13 @@ xt_status xt_ctx_stats(xt_ctx* ctx, xt_stats* out) {
     if (e != cudaSuccess) return cuda_fail(ctx, e, "event timing");
     ms += t;
   }
+  for (auto* c : ctx->chunk_ctx)
+    if (c) {
+      ctx->calls += c->calls;
+      ctx->launches += c->launches;
+      ctx->dp_launches += c->dp_launches;
+      c->calls = c->launches = c->dp_launches = 0;
+    }
   out->calls = ctx->calls;
   out->launches = ctx->launches;
   out->dp_launches = ctx->dp_launches;

@@ -173,5 +173,8 @@ struct xt_ctx {
   std::string last_error;
   std::string launch_error;      // which launch of the call failed
   xt::PendingCall pending;       // xt_extend_batch_begin .. _finish
+  // host-buffer calls in chunks: two internal contexts the chunks alternate
+  // between (created on first use, contexts without a memory budget only)
+  struct xt_ctx* chunk_ctx[2] = {};
 };
 

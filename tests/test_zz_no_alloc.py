@@ -117,3 +117,55 @@ def test_static_at_its_pair_limit():
         torch.cuda.synchronize()
         assert np.array_equal(out.cpu().numpy(), want_out), f"call {k}: results differ"
         assert np.array_equal(cells.cpu().numpy(), want_cells), f"call {k}: cells differ"
+
+
+def _capture_static(graph, args, n, sc, out, cells, stream):
+    """Capture one static call into `graph`; the call's host-side arguments
+    (its batch descriptor included) live in this frame only."""
+    import torch
+    import paper_2301_09310_gb300 as xt
+    q_seq, q_off, q_len, t_seq, t_off, t_len, h0 = args
+    with torch.cuda.graph(graph, stream=stream, capture_error_mode="thread_local"):
+        s = xt.xt_extend_batch_static(q_seq.data_ptr(), q_seq.numel(), q_off.data_ptr(),
+                                      q_len.data_ptr(), t_seq.data_ptr(), t_seq.numel(),
+                                      t_off.data_ptr(), t_len.data_ptr(), h0.data_ptr(), n, sc,
+                                      out.data_ptr(), cells.data_ptr(), stream.cuda_stream)
+    return s
+
+
+def test_static_replays_from_a_captured_graph():
+    # the documented use under stream capture: a first call outside capture,
+    # then a captured call whose graph replays after the capturing frame is gone
+    import torch
+    import paper_2301_09310_gb300 as xt
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    wl = synth.WORKLOADS["c3_mixed"]
+    b = synth.generate(wl, n=20000)
+    args = to_dev(b, dev)
+    ctx = xt.Context(0)
+    try:
+        want_out, want_cells = ctx.extend(*args, wl.scoring)
+        torch.cuda.synchronize()
+        want_out, want_cells = want_out.cpu().numpy(), want_cells.cpu().numpy()
+    finally:
+        ctx.close()
+    stream = torch.cuda.Stream(dev)
+    s, _, _ = _static_call(args, b.n, wl.scoring, stream)
+    assert s == xt.XT_OK, xt.xt_status_str(s)
+    torch.cuda.synchronize()
+    out = torch.empty((b.n, 7), dtype=torch.int32, device=dev)
+    cells = torch.empty(b.n, dtype=torch.int64, device=dev)
+    graph = torch.cuda.CUDAGraph()
+    s = _capture_static(graph, args, b.n, wl.scoring, out, cells, stream)
+    assert s == xt.XT_OK, xt.xt_status_str(s)
+    for k in range(2):
+        out.fill_(-7)
+        cells.fill_(-7)
+        torch.cuda.synchronize()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), want_out), f"replay {k}: results differ"
+        assert np.array_equal(cells.cpu().numpy(), want_cells), f"replay {k}: cells differ"
