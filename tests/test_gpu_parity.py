@@ -212,6 +212,34 @@ def test_host_variant_in_chunks(ctx):
                                                                            want_dev[1][keep])
 
 
+def test_host_chunks_under_a_budget(ctx):
+    # a context with a memory budget runs its chunks one after another on its
+    # own workspace (a context without one spreads them over two internal
+    # contexts): both must return the device call's results
+    import torch
+    import paper_2301_09310_gb300 as xt
+    wl = synth.WORKLOADS["c3_mixed"]
+    b = synth.generate(wl, n=2_100_000, first=4242)
+    want = run_gpu(ctx, b, wl.scoring)
+
+    def pinned(a):
+        t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
+        t.numpy()[...] = a
+        return t.numpy()
+
+    h = [pinned(a) for a in (b.q_seq, b.q_off, b.q_len, b.t_seq, b.t_off, b.t_len, b.h0)]
+    budgeted = xt.Context(0, mem_budget_bytes=16 << 30)
+    try:
+        for _ in range(2):
+            out, cells = budgeted.extend_host(*h, wl.scoring)
+            assert_same((out, cells), want, "chunked host call under a budget")
+    finally:
+        budgeted.close()
+    for _ in range(2):
+        out, cells = ctx.extend_host(*h, wl.scoring)
+        assert_same((out, cells), want, "chunked host call on chunk contexts")
+
+
 def test_repeat_calls_reuse_workspace(ctx):
     wl = synth.WORKLOADS["c2_short"]
     b1 = synth.generate(wl, n=2000, first=0)
