@@ -517,6 +517,9 @@ xt_status xt_extend_batch_static(const uint8_t* q_seq, int64_t q_bytes, const in
  * max_queued_bytes, xt_serve_submit returns XT_EBUSY and the caller retries.
  * Device memory: slots x (staging + result buffers + context workspace);
  * mem_budget_bytes caps the total (XT_ENOMEM at create or in a batch).
+ * The slots' contexts launch directly, without CUDA graphs: batches of a
+ * stream differ in their plans, and capturing a graph for each new plan
+ * would add to that batch's latency.
  */
 typedef struct xt_server xt_server;
 
