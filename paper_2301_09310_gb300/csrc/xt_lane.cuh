@@ -420,7 +420,7 @@ __device__ __forceinline__ void fold_keys(uint32_t (&K)[R], int32_t (&Blo)[R], i
 // by exact query length, so the 32 pairs of a warp share one geometry) and a
 // lane whose pair is done, or has no pair (valid = false), idles masked.
 // mshift = k with 2^k >= match + 1.  The caller guarantees, with B = h0 +
-// match*min(qlen,tlen): (B + 1) << k <= 32767, B * 32 + 31 <= 32767,
+// match*min(qlen,tlen): (B + 1) << k <= 32767, B * 64 + 63 <= 32767 (the row keys),
 // 1 <= qlen <= 65535 and tlen >= 1.
 template <int R, bool STAGED>
 __device__ __forceinline__ Outcome lane_pair_p16(const Pair& pr, bool valid, const Score& sc,
