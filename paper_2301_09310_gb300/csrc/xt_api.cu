@@ -261,8 +261,10 @@ constexpr size_t kLaneSmemCap = 48 * 1024;
 // needs a global ring and those are not allowed.
 bool lane_launch(xt_ctx* ctx, const Score& sc, int cls, int j, bool allow_gring, Launch* L) {
   const BucketSched* t = tuned(ctx, sc.w, j);
-  const int R = ctx->forced_P == 1 ? ctx->forced_R
-                                    : (t && t->P == 1 ? t->R : lane_default_R(j));
+  int R = ctx->forced_P == 1 ? ctx->forced_R : (t && t->P == 1 ? t->R : lane_default_R(j));
+  // the packed engine's 16-row strips need more registers than it has (they
+  // spill); its long buckets, and those with 4-bit row-key tags, keep 8
+  if (cls == CLS_PACKED && R > 8 && (ctx->forced_P != 1 || packed_tag_bits(j) == 4)) R = 8;
   const int rows = cls == CLS_PACKED ? 2 * R : R;
   const int64_t need = std::min<int64_t>((int64_t)1 << j, next_pow2(rows + 2 * (int64_t)sc.w + 2));
   const int lg = log2_ceil(need);
@@ -277,7 +279,8 @@ bool lane_launch(xt_ctx* ctx, const Score& sc, int cls, int j, bool allow_gring,
   L->grid = ctx->num_sms * per_sm;
   int k = 0;
   while ((1 << k) < ctx->match + 1) ++k;
-  L->mparam = cls == CLS_PACKED ? k : ctx->match + 1;
+  // packed: the anchoring shift and, above it, the row keys' step-tag bits
+  L->mparam = cls == CLS_PACKED ? (k | packed_tag_bits(j) << 8) : ctx->match + 1;
   return true;
 }
 
@@ -356,8 +359,10 @@ inline double band_cells_est(double q, int w) {
 
 // Flags for classify: kJHuge where the default group ring does not fit
 // (band geometry only), kJPacked where a one-lane schedule is possible for
-// the bucket in either size class.  lane_ok[j]: that one-lane launch exists.
-void batched_flags(xt_ctx* ctx, const Score& sc, JFlags* jf, bool* lane_ok) {
+// the bucket in either size class, kJTag4 on such buckets of 511-base queries
+// and longer in calls of n >= kTag4MinPairs pairs.  lane_ok[j]: that one-lane
+// launch exists.
+void batched_flags(xt_ctx* ctx, const Score& sc, int32_t n, JFlags* jf, bool* lane_ok) {
   *jf = JFlags{};
   for (int j = 0; j < kNumJ; ++j) lane_ok[j] = false;
   const bool saved = ctx->plan_small;
@@ -378,7 +383,8 @@ void batched_flags(xt_ctx* ctx, const Score& sc, JFlags* jf, bool* lane_ok) {
     }
     lane_ok[j] = want && lane_launch(ctx, sc, CLS_PACKED, j, true, &L) &&
                  lane_launch(ctx, sc, CLS_NARROW, j, true, &L);
-    if (lane_ok[j]) jf->f[j] |= kJPacked;
+    if (lane_ok[j])
+      jf->f[j] |= kJPacked | (packed_tag_bits(j) == 4 && n >= kTag4MinPairs ? kJTag4 : 0);
     // the default rule's answer (tuned group schedules always fit, see
     // bucket_sched_ok, but a bucket's class must not depend on its count)
     const int fP = ctx->forced_P;
@@ -740,7 +746,7 @@ xt_status run_begin(xt_ctx* ctx, bool plain, const uint8_t* q_seq, int64_t q_byt
   if (!plain) {
     // classify and order with count-independent bucket flags, then bring the
     // pair count of every (class, bucket) back for the plan
-    batched_flags(ctx, pc.sc, &pc.jf, pc.lane_ok);
+    batched_flags(ctx, pc.sc, n, &pc.jf, pc.lane_ok);
     e = enqueue_front(pc.jf, pc.sc, scr->match, pc.w, pc.desc, pc.n_cap, stream);
     const size_t seg_bytes =
         (size_t)((const char*)(pc.w.seg_end + kNumClasses * kNumJ) - (const char*)pc.w.seg_begin);

@@ -75,8 +75,10 @@ __device__ __forceinline__ int classify_pair(const Batch& b, int32_t k, int32_t 
   const bool wide = bound > 32767 || ql > 65535;
   const uint8_t jf = s_jf[j];
   int cls = wide ? CLS_WIDE : CLS_NARROW;
-  // packed: the anchoring multiply and the 16-bit row keys (H * 64 + step) fit
-  if (!wide && (jf & kJPacked) && ((bound + 1) << mshift) <= 32767 && bound * 64 + 63 <= 32767)
+  // packed: the anchoring multiply and the 16-bit row keys (H * 2^bits + step) fit
+  const int64_t tag = (jf & kJTag4) ? 16 : 64;
+  if (!wide && (jf & kJPacked) && ((bound + 1) << mshift) <= 32767 &&
+      bound * tag + tag - 1 <= 32767)
     cls = CLS_PACKED;
   if ((jf & kJHuge) || (cls == CLS_WIDE && (jf & kJHugeWide))) cls = CLS_HUGE;
   *bin = (cls * kNumJ + j) * kNumSub + sub;
@@ -284,7 +286,7 @@ __global__ void __launch_bounds__(kQueueThreads)
 // Every lane extends whole pairs on its own; the warp takes consecutive queue
 // slots (one atomicAdd per warp per round), so neighbouring lanes get pairs
 // of nearly equal length.
-template <int R, bool PACKED, bool GRING, bool QSTAGE>
+template <int R, bool PACKED, bool GRING, bool QSTAGE, int TB = 6>
 __global__ void __launch_bounds__(kLaneThreads, 4)
     k_lane(const Batch* __restrict__ bd, Score sc, Work w, int cls, int j_lo, int j_hi,
            int head_id, int rs_log2, void* gring, int mparam, int qs_log2) {
@@ -340,8 +342,8 @@ __global__ void __launch_bounds__(kLaneThreads, 4)
     Outcome o;
     qs.g = pr.q;
     if (PACKED)
-      o = lane_pair_p16<R, QSTAGE>(pr, valid, sc, s_prof, *reinterpret_cast<Ring<true>*>(&ring),
-                                   mparam, qs);
+      o = lane_pair_p16<R, QSTAGE, TB>(pr, valid, sc, s_prof,
+                                       *reinterpret_cast<Ring<true>*>(&ring), mparam & 0xFF, qs);
     else
       o = lane_pair_i32<R, GRING>(pr, valid, sc, s_prof, *reinterpret_cast<Ring<false>*>(&ring),
                                   mparam, pipe);
@@ -726,12 +728,12 @@ size_t lane_pipe_bytes(int cls, bool global_ring) {
   return (global_ring && cls != CLS_PACKED) ? (size_t)kLaneThreads * kPipeD * sizeof(int2) : 0;
 }
 
-template <int R, bool PACKED, bool GRING, bool QSTAGE>
+template <int R, bool PACKED, bool GRING, bool QSTAGE, int TB = 6>
 static cudaError_t launch_lane_t(const Batch* b, const Score& sc, const Work& w, const Launch& L,
                                  int head_id, void* gring, cudaStream_t stream) {
   const size_t smem = (GRING ? 0 : kLaneThreads * lane_ring_bytes(L.cls, L.rs_log2)) +
                       (QSTAGE ? lane_stage_bytes(L.j_hi) : 0) + lane_pipe_bytes(L.cls, GRING);
-  auto kern = k_lane<R, PACKED, GRING, QSTAGE>;
+  auto kern = k_lane<R, PACKED, GRING, QSTAGE, TB>;
   cudaError_t e = raise_smem_limit(kern, smem);
   if (e != cudaSuccess) return e;
   kern<<<L.grid, kLaneThreads, smem, stream>>>(b, sc, w, L.cls, L.j_lo, L.j_hi, head_id,
@@ -743,6 +745,15 @@ cudaError_t launch_lane(const Batch* b, const Score& sc, const Work& w, const La
                         int head_id, void* gring, cudaStream_t stream) {
   const bool packed = L.cls == CLS_PACKED;
   const bool stage = packed && lane_stage_bytes(L.j_hi) > 0;
+  // packed long buckets (no query stage): row keys with 4-bit step tags
+  if (packed && (L.mparam >> 8) == 4) {
+    if (stage || (L.R != 4 && L.R != 8)) return cudaErrorInvalidValue;
+    if (L.R == 4)
+      return L.global_ring ? launch_lane_t<4, true, true, false, 4>(b, sc, w, L, head_id, gring, stream)
+                           : launch_lane_t<4, true, false, false, 4>(b, sc, w, L, head_id, gring, stream);
+    return L.global_ring ? launch_lane_t<8, true, true, false, 4>(b, sc, w, L, head_id, gring, stream)
+                         : launch_lane_t<8, true, false, false, 4>(b, sc, w, L, head_id, gring, stream);
+  }
 #define XT_LG(RR, PK, GR)                                                                       \
   return stage ? launch_lane_t<RR, PK, GR, true>(b, sc, w, L, head_id, gring, stream)           \
                : launch_lane_t<RR, PK, GR, false>(b, sc, w, L, head_id, gring, stream);

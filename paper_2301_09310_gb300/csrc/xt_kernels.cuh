@@ -19,6 +19,18 @@ constexpr int kNumClasses = 4;           // classes that need a DP kernel
 constexpr uint8_t kJHuge = 1;            // bucket's pairs go to the HUGE class
 constexpr uint8_t kJPacked = 2;          // bucket runs the one-lane engine: packed pairs allowed
 constexpr uint8_t kJHugeWide = 4;        // the bucket's WIDE pairs (group engine only) are HUGE
+constexpr uint8_t kJTag4 = 8;            // packed row keys of the bucket carry 4-bit step tags
+// Step-tag bits of the packed row keys (H * 2^bits + step in 16 bits) in
+// bucket j: 6 (H <= 511) up to queries of 510 bases, 4 (H <= 2047, folded
+// every 16 steps) beyond, where a pair's score bound grows past 511.
+constexpr int kTag4J = 10;
+constexpr int packed_tag_bits(int j) { return j >= kTag4J ? 4 : 6; }
+// Calls of at least this many pairs pack those buckets' pairs (kJTag4): only
+// then are there enough of them to run one lane per pair; in smaller calls
+// they go to lane groups, which run them in 32-bit anyway (c5-mix calls:
+// 800k pairs 16.43 -> 16.00 ms, 4M 68.1 -> 58.8 ms; 400k 9.76 -> 11.90 ms had
+// they been packed: a second group launch waited for the first).
+constexpr int32_t kTag4MinPairs = 1 << 19;
 constexpr int kJMin = 5;                 // length buckets j: qlen + 2 <= 2^j
 constexpr int kJMax = 21;
 constexpr int kNumJ = kJMax + 1;

@@ -324,12 +324,11 @@ __device__ __forceinline__ Outcome lane_pair_i32(const Pair& pr, bool valid, con
 }
 
 // ------------------------------------------------------------- packed lane
-// Row maximum in packed form: within blocks of kTagSteps = 64 steps each half
-// keeps key = H * 64 + (step within the block), so one packed max keeps the
+// Row maximum in packed form: within blocks of 2^TB steps each half keeps
+// key = H * 2^TB + (step within the block), so one packed max keeps the
 // largest H with the latest (largest) column; at the end of a block the keys
-// are folded into 32-bit (H << 16 | column) per row.  Needs H <= 510.
-constexpr int kTagBits = 6;
-constexpr int kTagSteps = 1 << kTagBits;
+// are folded into 32-bit (H << 16 | column) per row.  TB = 6 needs H <= 511,
+// TB = 4 (a fold every 16 steps) H <= 2047.
 constexpr uint32_t kKeyNone = 0x80008000u;  // -32768 in both halves: no key yet
 
 // One step of the two stacked strips: the lower strip (low halves) at column
@@ -345,7 +344,7 @@ constexpr uint32_t kKeyNone = 0x80008000u;  // -32768 in both halves: no key yet
 //     finished) keep their state.
 // sel[r]: byte selector of row r in bits 0-15; bits 16-23 / 24-31 are 0xFF
 // when the lower / upper strip's target base is N (score n_score).
-template <int R, bool MASKED, bool HAS_N, bool KEEP>
+template <int R, bool MASKED, bool HAS_N, bool KEEP, int TB = 6>
 __device__ __forceinline__ void lane_step_p16(uint32_t (&Hl)[R], uint32_t (&HAl)[R],
                                               uint32_t (&El)[R], uint32_t (&K)[R],
                                               const uint32_t (&sel)[R], uint32_t prof_lo,
@@ -375,8 +374,9 @@ __device__ __forceinline__ void lane_step_p16(uint32_t (&Hl)[R], uint32_t (&HAl)
       H &= bm;
       F &= bm;
     }
-    // H * 64 + step, both halves at once (halves >= 0, below 2^9: no carry)
-    asm("max.s16x2 %0, %0, %1;" : "+r"(K[r]) : "r"(H * (uint32_t)kTagSteps + pos2));
+    // H * 2^TB + step, both halves at once (halves >= 0 and small enough that
+    // neither carries into the other)
+    asm("max.s16x2 %0, %0, %1;" : "+r"(K[r]) : "r"(H * (uint32_t)(1 << TB) + pos2));
     const uint32_t HA = add16x2(H, na2);
     D = Hleft;
     if (KEEP) {
@@ -402,15 +402,15 @@ __device__ __forceinline__ uint32_t bit_range(int32_t lo, int32_t hi, int n) {
 
 // Fold the block keys into the per-row (H << 16 | column) maxima; cbase is
 // the lower strip's column of block step 0 (the upper strip's is cbase - 1).
-template <int R>
+template <int R, int TB>
 __device__ __forceinline__ void fold_keys(uint32_t (&K)[R], int32_t (&Blo)[R], int32_t (&Bhi)[R],
                                           int32_t cbase) {
+  constexpr int32_t kMask = (1 << TB) - 1;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int32_t kl = lo16(K[r]), kh = hi16(K[r]);
-    if (kl >= 0) Blo[r] = max(Blo[r], ((kl >> kTagBits) << 16) | (cbase + (kl & (kTagSteps - 1))));
-    if (kh >= 0)
-      Bhi[r] = max(Bhi[r], ((kh >> kTagBits) << 16) | (cbase - 1 + (kh & (kTagSteps - 1))));
+    if (kl >= 0) Blo[r] = max(Blo[r], ((kl >> TB) << 16) | (cbase + (kl & kMask)));
+    if (kh >= 0) Bhi[r] = max(Bhi[r], ((kh >> TB) << 16) | (cbase - 1 + (kh & kMask)));
     K[r] = kKeyNone;
   }
 }
@@ -420,9 +420,9 @@ __device__ __forceinline__ void fold_keys(uint32_t (&K)[R], int32_t (&Blo)[R], i
 // by exact query length, so the 32 pairs of a warp share one geometry) and a
 // lane whose pair is done, or has no pair (valid = false), idles masked.
 // mshift = k with 2^k >= match + 1.  The caller guarantees, with B = h0 +
-// match*min(qlen,tlen): (B + 1) << k <= 32767, B * 64 + 63 <= 32767 (the row keys),
+// match*min(qlen,tlen): (B + 1) << k <= 32767, (B + 1) * 2^TB - 1 <= 32767 (the row keys),
 // 1 <= qlen <= 65535 and tlen >= 1.
-template <int R, bool STAGED>
+template <int R, bool STAGED, int TB = 6>
 __device__ __forceinline__ Outcome lane_pair_p16(const Pair& pr, bool valid, const Score& sc,
                                                  const uint32_t* s_prof, const Ring<true>& ring,
                                                  int mshift, Query<STAGED> qs) {
@@ -433,6 +433,7 @@ __device__ __forceinline__ Outcome lane_pair_p16(const Pair& pr, bool valid, con
   const uint32_t nn2 = pack16(nsc, nsc);
   // halves are >= 0 and below 2^(15-k): a 32-bit multiply by 2^k shifts each half
   const uint32_t mcm = 1u << mshift;
+  constexpr int32_t kTagSteps = 1 << TB;  // steps per row-key block
   constexpr int RR = 2 * R;
   constexpr int32_t kFar = 1 << 30;
   RowState st;
@@ -533,7 +534,7 @@ __device__ __forceinline__ Outcome lane_pair_p16(const Pair& pr, bool valid, con
           (lo_act ? bit_range(d0 - w, min(d0 + w, tlen - 1 - i0), R) : 0u) |
           ((hi_act ? bit_range(dh - w, min(dh + w, tlen - 1 - i0 - R), R) : 0u) << 16);
       const uint32_t keep = (lo_act ? 0u : 0x0000FFFFu) | (hi_act ? 0u : 0xFFFF0000u);
-      lane_step_p16<R, true, true, true>(Hl, HAl, El, K, sel, prof, prof_prev, nn2, D, Hup, Fup,
+      lane_step_p16<R, true, true, true, TB>(Hl, HAl, El, K, sel, prof, prof_prev, nn2, D, Hup, Fup,
                                          pos2, na2, nb2, mcm, inband, keep, oH, oF);
       if (hi_act) ring.at(c - 1) = prmt(oH, oF, 0x7632u);
       oH2 = oH1;
@@ -549,7 +550,7 @@ __device__ __forceinline__ Outcome lane_pair_p16(const Pair& pr, bool valid, con
       ring_n1 = ring_n2;
       ring_n2 = ring_n3;
       if (++blk == kTagSteps) {
-        fold_keys<R>(K, Blo, Bhi, cbase);
+        fold_keys<R, TB>(K, Blo, Bhi, cbase);
         cbase += kTagSteps;
         blk = 0;
       }
@@ -574,7 +575,7 @@ __device__ __forceinline__ Outcome lane_pair_p16(const Pair& pr, bool valid, con
       // faster than a vote between two copies of the step: the instruction
       // cache, not the ALU count, decides here
       uint32_t oH, oF;
-      lane_step_p16<R, false, true, false>(Hl, HAl, El, K, sel, prof_c, prof_prev, nn2, D, Hup,
+      lane_step_p16<R, false, true, false, TB>(Hl, HAl, El, K, sel, prof_c, prof_prev, nn2, D, Hup,
                                            Fup, pos2, na2, nb2, mcm, 0u, 0u, oH, oF);
       ring.at(c - 1) = prmt(oH, oF, 0x7632u);
       oH2 = oH1;
@@ -602,7 +603,7 @@ __device__ __forceinline__ Outcome lane_pair_p16(const Pair& pr, bool valid, con
 #pragma unroll kFastUnroll
         for (; s <= e; ++s) fast_step(s);
         if (blk == kTagSteps) {
-          fold_keys<R>(K, Blo, Bhi, cbase);
+          fold_keys<R, TB>(K, Blo, Bhi, cbase);
           cbase += kTagSteps;
           blk = 0;
         }
@@ -611,7 +612,7 @@ __device__ __forceinline__ Outcome lane_pair_p16(const Pair& pr, bool valid, con
         ++s;
       }
     }
-    fold_keys<R>(K, Blo, Bhi, cbase);
+    fold_keys<R, TB>(K, Blo, Bhi, cbase);
     hi_prev = hi;
     if (live) {
       int32_t last_m = 0;
