@@ -107,3 +107,33 @@ def test_c4_full_batch_sampled_against_oracle(ctx):
     assert bad.size == 0, (f"{bad.size} of 2000 sampled pairs differ; first pair "
                            f"#{idx[bad[0]]}: gpu {got_out[bad[0]].tolist()} cells {got_cells[bad[0]]}"
                            f" oracle {want_out[bad[0]].tolist()} cells {want_cells[bad[0]]}")
+
+
+def test_c5_long_queries_packed_with_short_tags(ctx):
+    """A 600,000-pair call of the c5 mix: at 2^19 pairs and more, queries of
+    511 bases and longer (h0 + match * length above 511) run packed with
+    4-bit row-key tags.  1,500 of them and 500 other pairs are compared with
+    the oracle on every field and on cells, and every pair must equal the
+    same pairs extended in two calls of 300,000 (below that size the long
+    queries take the 32-bit engines)."""
+    wl = synth.WORKLOADS["c5_stream"]
+    b = synth.generate(wl, n=600_000)
+    out, cells = run_gpu(ctx, b, wl.scoring)
+    check_properties(b, out, cells, wl.scoring)
+    rng = np.random.default_rng(2305)
+    long_ = np.nonzero(b.q_len >= 511)[0]
+    assert long_.size > 1500
+    idx = np.unique(np.concatenate([rng.choice(long_, size=1500, replace=False),
+                                    rng.choice(b.n, size=500, replace=False)]))
+    sub = b.take(idx)
+    want_out, want_cells = run_oracle(sub, wl.scoring)
+    got_out, got_cells = out[idx], cells[idx]
+    bad = np.nonzero(np.any(got_out != want_out, axis=1) | (got_cells != want_cells))[0]
+    assert bad.size == 0, (f"{bad.size} of {idx.size} sampled pairs differ; first pair "
+                           f"#{idx[bad[0]]}: gpu {got_out[bad[0]].tolist()} cells {got_cells[bad[0]]}"
+                           f" oracle {want_out[bad[0]].tolist()} cells {want_cells[bad[0]]}")
+    half = b.n // 2
+    for lo, hi in ((0, half), (half, b.n)):
+        part = b.take(np.arange(lo, hi))
+        pout, pcells = run_gpu(ctx, part, wl.scoring)
+        assert np.array_equal(pout, out[lo:hi]) and np.array_equal(pcells, cells[lo:hi])
