@@ -712,7 +712,10 @@ static cudaError_t launch_queue_w(const Batch* b, const Score& sc, const Work& w
 
 cudaError_t launch_queue(const Batch* b, const Score& sc, const Work& w, const Launch& L,
                          int head_id, int2* gring, cudaStream_t stream) {
-  if (L.cls == CLS_NARROW) return launch_queue_w<false>(b, sc, w, L, head_id, gring, stream);
+  // packed pairs (score bound B <= 2047) fit the 32-bit row key H * 65536 + j
+  // as NARROW pairs do; WIDE and HUGE pairs keep the explicit (max, column)
+  if (L.cls == CLS_NARROW || L.cls == CLS_PACKED)
+    return launch_queue_w<false>(b, sc, w, L, head_id, gring, stream);
   return launch_queue_w<true>(b, sc, w, L, head_id, gring, stream);
 }
 
