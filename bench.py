@@ -24,6 +24,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import gc
 import json
 import os
 import statistics
@@ -980,6 +981,10 @@ def serve_levels(args, local, b, wl, peak_pairs, ref_out, ref_cells, total_cells
                 bpairs[r] = tm.batch_pairs
 
         th = threading.Thread(target=waiter)
+        # no garbage-collection pauses in the load generator: a late submit
+        # counts as latency (from the scheduled arrival)
+        gc_on = gc.isenabled()
+        gc.disable()
         th.start()
         t0 = time.monotonic_ns() + 5_000_000
         arrive = t0 + (rs.arrival_s * 1e9).astype(np.int64)
@@ -1008,6 +1013,8 @@ def serve_levels(args, local, b, wl, peak_pairs, ref_out, ref_cells, total_cells
                 raise RuntimeError(f"xt_serve_submit: {xt.xt_status_str(s)}")
             tickets.put(tk.value)
         th.join()
+        if gc_on:
+            gc.enable()
         st = xt.xt_serve_get_stats(srv)
         xt.xt_serve_destroy(srv)
         if status:

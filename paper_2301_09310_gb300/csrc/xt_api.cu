@@ -101,6 +101,7 @@ xt_status xt::ctx_alloc(xt_ctx* ctx, void** p, size_t* have, size_t want) {
   return dev_alloc(ctx, p, have, want);
 }
 
+
 xt_status xt::ctx_codes(xt_ctx* ctx, const uint8_t** q_seq, int64_t* q_bytes,
                         const uint8_t** t_seq, int64_t* t_bytes, cudaStream_t stream) {
   if (ctx->alphabet == XT_ALPHABET_CODES) return XT_OK;
@@ -560,6 +561,36 @@ size_t layout_pool(const xt_ctx* ctx, Plan* pl) {
 }
 
 }  // namespace
+
+// Size a context's device buffers once for calls of up to n_pairs pairs: the
+// workspace of that capacity class, the global ring pool to pool_bytes (at
+// most its cap, as far as the budget allows; a plan that needs more grows it
+// later) and, when conv_bytes > 0, the buffer of converted sequences.  A
+// long-running caller (the server's slots) then does not free and regrow them
+// between calls: a cudaFree waits for the whole device.
+xt_status xt::ctx_reserve(xt_ctx* ctx, int32_t n_pairs, size_t conv_bytes, size_t pool_bytes) {
+  if (!ctx || n_pairs < 0) return XT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, XT_ECUDA, "cudaSetDevice");
+  int lg = 10;
+  while (lg < 31 && (1 << lg) < n_pairs) ++lg;
+  Work w;
+  Batch* desc = nullptr;
+  xt_status s = get_work(ctx, lg >= 31 ? INT32_MAX : (1 << lg), &w, &desc);
+  if (s == XT_OK && conv_bytes) s = dev_alloc(ctx, &ctx->conv, &ctx->conv_bytes, conv_bytes);
+  if (s != XT_OK) return s;
+  size_t pool = std::min(pool_bytes, kPoolCap);
+  if (ctx->budget) {
+    const size_t left = ctx->budget > ctx->held ? ctx->budget - ctx->held : 0;
+    pool = std::min(pool, ctx->pool_bytes + left);
+  }
+  if (pool > ctx->pool_bytes) {
+    void* old = ctx->pool;
+    s = dev_alloc(ctx, (void**)&ctx->pool, &ctx->pool_bytes, pool);
+    if (ctx->pool != old) drop_graphs(ctx);
+  }
+  return s;
+}
 
 bool xt::bucket_sched_ok(const xt_ctx* ctx, int w, int j, int P, int R) {
   if (j < kJMin || j > kJMax || w < 0) return false;

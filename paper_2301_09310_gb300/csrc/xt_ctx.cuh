@@ -63,6 +63,9 @@ xt_status ctx_fail(struct ::xt_ctx* ctx, xt_status s, const char* msg);
 xt_status ctx_cuda_fail(struct ::xt_ctx* ctx, cudaError_t e, const char* where);
 // Grow *p (holding *have bytes) to at least `want` bytes within the budget.
 xt_status ctx_alloc(struct ::xt_ctx* ctx, void** p, size_t* have, size_t want);
+// Size the workspace, the ring pool (to pool_bytes) and (conv_bytes > 0) the
+// conversion buffer for calls of up to n_pairs pairs once (see xt_api.cu).
+xt_status ctx_reserve(struct ::xt_ctx* ctx, int32_t n_pairs, size_t conv_bytes, size_t pool_bytes);
 // With the ASCII or the 4-bit alphabet, convert both sequence buffers to one
 // base code per byte in the context's workspace, point *q_seq / *t_seq at
 // them and set *q_bytes / *t_bytes to their sizes in bases (no-op for codes).

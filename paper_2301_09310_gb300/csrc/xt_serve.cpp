@@ -26,6 +26,11 @@
 
 #include "xt.h"
 
+namespace xt {
+// sizes a context's device buffers once for calls of up to n_pairs pairs (xt_api.cu)
+xt_status ctx_reserve(xt_ctx* ctx, int32_t n_pairs, size_t conv_bytes, size_t pool_bytes);
+}  // namespace xt
+
 namespace {
 
 constexpr int64_t kPairInBytes = 28;   // staged per pair: q_off, t_off (int64), q_len, t_len, h0
@@ -471,6 +476,14 @@ xt_status xt_serve_create(xt_server** out, int device, const xt_serve_config* cf
     if (st == XT_OK) st = xt_ctx_set_graphs(s.ctx, 0);
     if (st == XT_OK && cfg.tuning_path) st = xt_ctx_load_tuning(s.ctx, cfg.tuning_path);
     if (st == XT_OK) st = xt_ctx_set_alphabet(s.ctx, cfg.alphabet);
+    // every buffer a batch can need, sized now: regrowing one mid-stream frees
+    // the old buffer, and a cudaFree waits for the other slots' work
+    // (ring pool: 1 GB holds the global rings of the c5 mix's plans, about
+    // 0.6 GB at most)
+    if (st == XT_OK)
+      st = xt::ctx_reserve(s.ctx, cfg.max_batch_pairs,
+                           cfg.alphabet == XT_ALPHABET_ASCII ? (size_t)S->in_cap + 4096 : 0,
+                           (size_t)1 << 30);
     cudaError_t e = st == XT_OK ? cudaSuccess : cudaErrorUnknown;
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&s.start_ev);
