@@ -240,6 +240,23 @@ def test_host_chunks_under_a_budget(ctx):
         assert_same((out, cells), want, "chunked host call on chunk contexts")
 
 
+def test_shared_ring_pool_under_a_budget(ctx):
+    # a 1M-pair call of the c5 mix runs several global-ring launches: with no
+    # budget each has a pool region of its own and they run side by side; a
+    # 400 MB budget holds the largest of them but not their sum, so they
+    # share one region and run one after another.  Both give the same results.
+    import paper_2301_09310_gb300 as xt
+    wl = synth.WORKLOADS["c5_stream"]
+    b = synth.generate(wl, n=1_000_000, first=77)
+    want = run_gpu(ctx, b, wl.scoring)
+    budgeted = xt.Context(0, mem_budget_bytes=400 << 20)
+    try:
+        for _ in range(2):
+            assert_same(run_gpu(budgeted, b, wl.scoring), want, "shared ring pool")
+    finally:
+        budgeted.close()
+
+
 def test_repeat_calls_reuse_workspace(ctx):
     wl = synth.WORKLOADS["c2_short"]
     b1 = synth.generate(wl, n=2000, first=0)
